@@ -1,0 +1,391 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 permanent engine.
+
+Workload: the plain single-permanent sweep — complex128 n x n matrices with
+i.i.d. circular Gaussian entries of variance 1/n^2 (the collision-free n-photon
+submatrix of an m = n^2 mode Haar unitary), Glynn and Ryser Gray-code sums in
+FP64, one matrix per launch.  One step = one permanent per (method, n) with the
+seed cycling 0, 1, 2 over the steps.  Metric: Gray-code terms per second
+(Glynn 2^(n-1) terms, Ryser 2^n terms), device-timed with CUDA events, inputs
+resident in HBM; the L2 (129 MB) is flushed between steps by writing 256 MB.
+
+The JSON line also carries: the end-to-end rate through the C ABI from pinned
+host buffers (copies inside the timed region), the roofline of the dominant
+kernel against the FP64 peak derived from SM count x 4 FP64 flop/clk/SM x max
+SM clock, the SM clocks sampled during the timed region, and the CPU oracle's
+rate on a bounded sample (rank 0, N = 1).
+
+``--impl reference`` times the CPU oracle (the only reference implementation of
+this method here) on the same workload, one bounded sample per item and step.
+
+Multi-GPU (torchrun): every rank runs the same sweep on its own GPU — the
+permanents are independent problems, so there is no data-path collective; the
+step time is the max over ranks and ``value`` counts the terms of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gray-code terms/s (plain FP64 Glynn + Ryser permanents)"
+UNIT = "terms/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n-list", default="24,28,32", help="matrix sizes of the sweep")
+    ap.add_argument("--kinds", default="glynn,ryser")
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp64_dd", "fp32p_dd"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def terms_of(kind: str, n: int) -> int:
+    return 2 ** (n - 1) if kind == "glynn" else 2 ** n
+
+
+def flops_per_term(n: int) -> int:
+    # update 2n + product 6(n-1) + accumulate 2 (FP64 flops per Gray-code term)
+    return 8 * n - 4
+
+
+def workload(args):
+    ns = [int(x) for x in args.n_list.split(",") if x]
+    kinds = [k for k in args.kinds.split(",") if k]
+    return ns, kinds
+
+
+def step_items(ns, kinds, step):
+    seed = step % 3
+    return [(k, n, seed) for n in ns for k in kinds]
+
+
+def config_dict(args, ns, kinds, world):
+    return {
+        "workload": "plain single-permanent sweep: complex128 Gaussian var 1/n^2, n=%s, %s, %s, "
+                    "seed cycling 0,1,2 over steps, one matrix per launch" % (
+                        ",".join(map(str, ns)), "+".join(kinds), args.prec),
+        "n": ns,
+        "methods": kinds,
+        "precision_rung": args.prec,
+        "l2": "flushed between steps (256 MB write); inputs 16 n^2 bytes",
+        "parallelism": "independent permanents per GPU (x%d)" % world,
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(p[1]), smax=float(p[2]), power=float(p[3]), hw=p[5], hwt=p[6], swt=p[7],
+                                 swp=p[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                              ("swp", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(r["power"] for r in rows)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores
+# ---------------------------------------------------------------------------
+def oracle_rate(items, seconds: float, threads: int):
+    """Oracle terms/s over bounded Gray-index samples of the given items."""
+    import oracle
+    import synthetic as S
+
+    mats = {(n, seed): S.gaussian(n, seed) for _, n, seed in items}
+
+    def run(sample):
+        t0 = time.perf_counter()
+        done = 0
+        for kind, n, seed in items:
+            cnt = min(sample, terms_of(kind, n))
+            f = oracle.glynn_range if kind == "glynn" else oracle.ryser_range
+            f(mats[(n, seed)], 0, cnt, gray=True, threads=threads)
+            done += cnt
+        return done, time.perf_counter() - t0
+
+    sample = 64
+    done, dt = run(sample)
+    while dt < seconds / 8 and sample < (1 << 40):
+        sample *= 2
+        done, dt = run(sample)
+    if dt < seconds:
+        sample = int(sample * seconds / max(dt, 1e-6))
+        done, dt = run(sample)
+    return done / dt, sample, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    ns, kinds = workload(args)
+    threads = os.cpu_count() or 1
+    per_step = max(args.cpu_seconds, 1.0) / 3.0
+    # calibrate one bounded sample per item so that a step costs ~per_step seconds
+    items0 = step_items(ns, kinds, 0)
+    _, sample, _ = oracle_rate(items0, per_step / 4, threads)
+    import oracle
+    import synthetic as S
+
+    def one_step(step):
+        items = step_items(ns, kinds, step)
+        t0 = time.perf_counter()
+        done = 0
+        for kind, n, seed in items:
+            cnt = min(sample, terms_of(kind, n))
+            f = oracle.glynn_range if kind == "glynn" else oracle.ryser_range
+            f(S.gaussian(n, seed), 0, cnt, gray=True, threads=threads)
+            done += cnt
+        return done, time.perf_counter() - t0
+
+    for w in range(args.warmup):
+        one_step(w)
+    tot_terms, tot_t = 0, 0.0
+    for s in range(args.steps):
+        d, t = one_step(s)
+        tot_terms += d
+        tot_t += t
+    value = tot_terms / tot_t
+    sample_desc = ("oracle quad-precision Gray-order partial sums, first %d terms of each (method, n) item per step"
+                   % sample)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f128 (oracle)",
+        "data": "synthetic", "config": config_dict(args, ns, kinds, 1),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample_desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    import paper_1606_05836_gb300 as pg
+    import synthetic as S
+
+    rank, world, local = dist_env()
+    if world != args.gpus:
+        raise SystemExit("--gpus %d but WORLD_SIZE=%d" % (args.gpus, world))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    pg.library()
+    ns, kinds = workload(args)
+    fn = {"glynn": pg.glynn, "ryser": pg.ryser}
+    host = {(n, seed): S.gaussian(n, seed) for n in ns for seed in range(3)}
+    dmat = {key: torch.as_tensor(a).to(dev) for key, a in host.items()}
+    pinned = {key: torch.as_tensor(a).pin_memory() for key, a in host.items()}
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    nmax = max(ns)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # warm-up (also compiles nothing: the library is prebuilt; first calls set attributes)
+    for w in range(args.warmup):
+        for kind, n, seed in step_items(ns, kinds, w):
+            fn[kind](dmat[(n, seed)], prec=args.prec)
+    torch.cuda.synchronize(dev)
+
+    # ---- device-timed steps ----
+    sampler = ClockSampler(local) if rank == 0 else None
+    barrier()
+    torch.cuda.synchronize(dev)
+    if sampler:
+        sampler.start()
+    step_ms = []
+    dom = []  # (flops, ms) of the dominant kernel's launches
+    terms_total = 0
+    launches = 0
+    for s in range(args.steps):
+        flush.zero_()
+        items = step_items(ns, kinds, s)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in items]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for (kind, n, seed), (a, b) in zip(items, ev):
+            a.record(stream)
+            fn[kind](dmat[(n, seed)], prec=args.prec)
+            b.record(stream)
+            terms_total += terms_of(kind, n)
+            launches += 1
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        step_ms.append(e0.elapsed_time(e1))
+        for (kind, n, seed), (a, b) in zip(items, ev):
+            if n == nmax:
+                dom.append((flops_per_term(n) * terms_of(kind, n), a.elapsed_time(b)))
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop() if sampler else None
+    t_dev = max_over_ranks(sum(step_ms) / 1e3)
+    barrier()
+
+    # ---- end-to-end steps: pinned host -> device, compute, result -> host ----
+    e2e = None
+    if not args.no_e2e:
+        out_host = torch.empty(1, dtype=torch.complex128).pin_memory()
+        h2d = d2h = 0
+        e2e_ms = []
+        e2e_terms = 0
+        barrier()
+        torch.cuda.synchronize(dev)
+        for s in range(args.steps):
+            flush.zero_()
+            items = step_items(ns, kinds, s)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h2d = d2h = 0
+            for kind, n, seed in items:
+                src = pinned[(n, seed)]
+                dA = src.to(dev, non_blocking=True)
+                r = fn[kind](dA, prec=args.prec)
+                out_host.copy_(r.reshape(1), non_blocking=True)
+                h2d += src.numel() * src.element_size()
+                d2h += out_host.numel() * out_host.element_size()
+                e2e_terms += terms_of(kind, n)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            e2e_ms.append(e0.elapsed_time(e1))
+        t_e2e = max_over_ranks(sum(e2e_ms) / 1e3)
+        e2e = {"value": world * e2e_terms / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        return 0
+
+    value = world * terms_total / t_dev
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    # GB300: 2 FP64 FMA lanes per clock per SM (0.5 per sub-partition) = 4 flop/clk/SM
+    peak_fp64 = sms * 4 * sm_max_mhz * 1e6
+    achieved = sum(f for f, _ in dom) / (sum(ms for _, ms in dom) / 1e3) if dom else None
+    roofline = {
+        "bound": "alu", "pipe": "fp64",
+        "kernel": "fwd_kernel<N=%d> (Glynn+Ryser, %s)" % (nmax, args.prec),
+        "achieved": achieved / 1e12 if achieved else None, "peak": peak_fp64 / 1e12, "unit": "TFLOP/s",
+        "frac": (achieved / peak_fp64) if achieved else None,
+        "peak_source": "derived: %d SMs x 4 FP64 flop/clk/SM x %.0f MHz" % (sms, sm_max_mhz),
+        "flops_per_term": "8n-4 (2n update + 6(n-1) product + 2 accumulate)",
+        "traffic": None,
+    }
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        items = step_items(ns, kinds, 0)
+        rate, sample, dt = oracle_rate(items, args.cpu_seconds, threads)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "quad-precision oracle, first %d Gray-order terms of each (method, n) item of step 0, "
+                         "%.1f s" % (sample, dt)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec != "fp32p_dd" else "f64+f32",
+        "data": "synthetic", "config": config_dict(args, ns, kinds, world), "roofline": roofline,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,139 @@
+/*
+ * perm.h — C ABI of libperm, a GB300 (sm_103a) engine for matrix permanents.
+ *
+ * The problem (arXiv 1606.05836, Eq. (1) and Supp. "Parallelization and
+ * Optimization"): the probability of a boson-sampling outcome is
+ *     Pr[S -> T] = |Per(U_ST)|^2 / (s_1! ... s_m! t_1! ... t_m!),
+ * and Per(A) of the n x n submatrix is evaluated by Ryser's formula (Supp.
+ * Eq. (S1)) or the BB/FG (Glynn) formula (Supp. Eq. (S2)).  The sums are walked
+ * in reflected-Gray-code order, so consecutive terms differ by one column.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Matrices are complex128, row-major, a[i][j] = A[i*lda + j], lda >= n, with
+ *   perm_c128 layout-compatible with C99 double _Complex / torch.complex128.
+ * - Every pointer named d* is DEVICE memory owned by the caller; the library
+ *   allocates no device memory.  Entry points that need scratch take a caller
+ *   workspace (query its size with the matching *_workspace function); pass a
+ *   16-byte-aligned buffer of at least that size.  The library never frees it.
+ * - Calls are asynchronous and stream-ordered on `stream` (a cudaStream_t;
+ *   NULL = the legacy default stream), except prob_sample which synchronises
+ *   the stream and returns a host value.  Two calls that share a workspace must
+ *   be ordered on one stream.
+ * - Host-detectable argument errors return a negative perm_status before
+ *   anything is launched; launch failures return PERM_ECUDA.  NaN/Inf entries
+ *   propagate to a non-finite result.  Nothing calls exit/abort and no kernel
+ *   waits on a flag, so no call can hang the device.
+ * - Gray index k in [0, 2^M) addresses one term.  Glynn: M = n-1, delta_1 = +1
+ *   and delta_{b+2} = -1 iff bit b of g(k) = k ^ (k >> 1) is set.  Ryser:
+ *   M = n, column b+1 is in the subset iff bit b of g(k) is set.
+ * - n <= PERM_MAX_N.  n = 0 gives Per = 1.
+ */
+#ifndef PERM_H_
+#define PERM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PERM_MAX_N 48
+#define PERM_ABI_VERSION 1
+
+typedef struct {
+  double re, im;
+} perm_c128;
+
+typedef enum {
+  PERM_OK = 0,
+  PERM_EINVAL = -1,     /* null pointer, bad lda/stride/option, bad occupation vector */
+  PERM_ERANGE = -2,     /* n < 0 or n > PERM_MAX_N, or an index range out of [0, 2^M) */
+  PERM_ENOMEM = -3,     /* workspace smaller than required */
+  PERM_ECUDA = -4,      /* a CUDA runtime call or launch failed (see perm_last_cuda_error) */
+  PERM_ENONFINITE = -5, /* non-finite value where a finite one is required */
+  PERM_ETIMEOUT = -6    /* reserved: a bounded wait ran out */
+} perm_status;
+
+/* Precision ladder.  FP64 is used in every rung for the Gray-code row-sum
+ * updates, the row sums recomputed at each chunk start and the cross-block
+ * reduction. */
+typedef enum {
+  PERM_FP64 = 0,    /* R0: FP64 products, FP64 accumulation of the terms */
+  PERM_FP64_DD = 1, /* R1: FP64 products, double-double accumulation of the terms */
+  PERM_FP32P_DD = 2 /* R2: FP32 n-way products of the FP64 row sums, double-double accumulation */
+} perm_prec;
+
+/* Launch options; pass NULL for the defaults (every field 0 = default). */
+typedef struct {
+  int prec;       /* perm_prec */
+  int chunk_log2; /* row sums are recomputed from scratch every 2^chunk_log2 steps (default 12, 1..30) */
+  int block;      /* threads per block (multiple of 32, 32..256; default 128) */
+  int grid;       /* blocks (default: SMs x resident blocks per SM) */
+  int unit_log2;  /* perm_batched: Gray indices per lane in one work unit, log2 (default 11, 0..30) */
+} perm_opts;
+
+/* --- single permanent ------------------------------------------------------ */
+
+/* Bytes of workspace needed by perm_glynn / perm_ryser / *_range for these
+ * options on the current device. */
+size_t perm_workspace_size(int n, const perm_opts* opts);
+
+/* Per(A) by the BB/FG (Glynn) formula, Supp. Eq. (S2) and Algorithm 2 of
+ * arXiv 1606.05836: all 2^(n-1) delta vectors, then / 2^(n-1).  dOut receives
+ * one perm_c128. */
+int perm_glynn(const perm_c128* dA, int n, int lda, perm_c128* dOut, void* dWork, size_t workBytes,
+               const perm_opts* opts, void* stream);
+
+/* Per(A) by Ryser's formula, Supp. Eq. (S1) and Algorithm 1: the 2^n subsets,
+ * then x (-1)^n.  dOut receives one perm_c128. */
+int perm_ryser(const perm_c128* dA, int n, int lda, perm_c128* dOut, void* dWork, size_t workBytes,
+               const perm_opts* opts, void* stream);
+
+/* Partial sums over Gray indices [k_begin, k_end) — the index-range split of
+ * Algorithms 1 and 2 (each MPI process took such a range) and the unit a
+ * multi-GPU shard computes.  The sum is of the un-normalised signed terms
+ * (no 1/2^(n-1), no (-1)^n).  dOut receives two perm_c128: the double-double
+ * sum as (hi, lo).  Requires n >= 1 and k_begin <= k_end <= 2^M. */
+int perm_glynn_range(const perm_c128* dA, int n, int lda, uint64_t k_begin, uint64_t k_end, perm_c128* dOut,
+                     void* dWork, size_t workBytes, const perm_opts* opts, void* stream);
+int perm_ryser_range(const perm_c128* dA, int n, int lda, uint64_t k_begin, uint64_t k_end, perm_c128* dOut,
+                     void* dWork, size_t workBytes, const perm_opts* opts, void* stream);
+
+/* --- batched permanents --------------------------------------------------- */
+
+/* Many permanents of mixed sizes 1 <= n_i <= PERM_BATCH_MAX_N in one persistent,
+ * size-bucketed launch (largest n first; items cut into work units that warps
+ * claim from a shared counter).  This is the batch of output patterns of one
+ * interferometer behind Eq. (1) of arXiv 1606.05836.
+ *
+ * dPacked:  all matrices, row-major, item i at dPacked + dOffsets[i] with lda = n_i.
+ * dOffsets: int64 offsets in complex elements (device), dN: int32 sizes (device);
+ * hN:       the same sizes on the host (used only to size the workspace layout).
+ * method:   0 = Glynn (Eq. (S2)), 1 = Ryser (Eq. (S1)).
+ * dScale:   nullable per-item factor for the probability, e.g. 1/(prod s_i! prod t_j!).
+ * dOut:     per-item Per (perm_c128).  dProb: nullable per-item |Per|^2 * scale.
+ * dWork:    256-byte-aligned workspace of perm_batched_workspace_size() bytes.
+ * If dN disagrees with hN so that the plan does not fit, or an n is out of
+ * range, the outputs are NaN (no out-of-bounds access).  All kernels are
+ * launched on `stream`; the sequence is graph-capturable.  Per item the result
+ * is deterministic for fixed options. */
+#define PERM_BATCH_MAX_N 32
+size_t perm_batched_workspace_size(int count, const int32_t* hN, int method, const perm_opts* opts);
+int perm_batched(const perm_c128* dPacked, const int64_t* dOffsets, const int32_t* dN, const int32_t* hN, int count,
+                 int method, const double* dScale, perm_c128* dOut, double* dProb, void* dWork, size_t workBytes,
+                 const perm_opts* opts, void* stream);
+
+/* --- diagnostics ----------------------------------------------------------- */
+
+const char* perm_strerror(int status);
+/* The cudaError_t of the most recent PERM_ECUDA on this host thread (0 if none). */
+int perm_last_cuda_error(void);
+int perm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PERM_H_ */

@@ -1,0 +1,112 @@
+"""GB300 (sm_103a) engine for matrix permanents — the boson-sampling hot path.
+
+Thin Python binding over the C ABI in ``include/perm.h`` (``libperm.so``):
+argument marshalling only.  Every step of the computation runs in the CUDA
+kernels of ``csrc/``; PyTorch is used for device memory and streams.  There is
+no CPU fallback: calls raise if the library is missing or no GPU is present.
+
+Functions mirror the C entry points:
+
+* :func:`glynn`  -- Per(A), BB/FG formula (Supp. Eq. (S2), Algorithm 2 of arXiv 1606.05836)
+* :func:`ryser`  -- Per(A), Ryser formula (Supp. Eq. (S1), Algorithm 1)
+* :func:`glynn_range`, :func:`ryser_range` -- partial sums over a Gray-index range
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _native
+from ._native import PERM_MAX_N, PRECISIONS, Opts, PermError
+
+__all__ = ["glynn", "ryser", "glynn_range", "ryser_range", "workspace_size", "PermError", "PERM_MAX_N",
+           "PRECISIONS", "library"]
+
+_workspaces: dict = {}
+
+
+def library():
+    """The loaded ctypes library (raises if libperm.so is missing)."""
+    return _native.load()
+
+
+def _opts(prec="fp64", chunk_log2=0, block=0, grid=0, unit_log2=0):
+    if isinstance(prec, str):
+        if prec not in PRECISIONS:
+            raise ValueError("prec must be one of %s" % sorted(PRECISIONS))
+        prec = PRECISIONS[prec]
+    return Opts(int(prec), int(chunk_log2), int(block), int(grid), int(unit_log2))
+
+
+def _matrix(A: torch.Tensor):
+    if not isinstance(A, torch.Tensor) or not A.is_cuda:
+        raise TypeError("A must be a CUDA tensor")
+    if A.dtype != torch.complex128:
+        raise TypeError("A must be complex128")
+    if A.dim() != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("A must be square, got %s" % (tuple(A.shape),))
+    n = A.shape[0]
+    if n > 0 and (A.stride(1) != 1 or A.stride(0) < n):
+        A = A.contiguous()
+    lda = A.stride(0) if n > 0 else 0
+    return A, n, max(lda, n)
+
+
+def _stream_ptr(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def workspace_size(n: int, **opts) -> int:
+    o = _opts(**opts)
+    return int(library().perm_workspace_size(int(n), ctypes.byref(o)))
+
+
+def _workspace(device, nbytes: int) -> torch.Tensor:
+    key = (device.index, _stream_ptr(device))
+    buf = _workspaces.get(key)
+    if buf is None or buf.numel() < nbytes:
+        buf = torch.empty(max(nbytes, 4096), dtype=torch.uint8, device=device)
+        _workspaces[key] = buf
+    return buf
+
+
+def _run(fname, A, extra, out_len, **opts):
+    lib = library()
+    A, n, lda = _matrix(A)
+    o = _opts(**opts)
+    dev = A.device
+    out = torch.empty(out_len, dtype=torch.complex128, device=dev)
+    ws_bytes = int(lib.perm_workspace_size(int(n), ctypes.byref(o)))
+    ws = _workspace(dev, ws_bytes)
+    with torch.cuda.device(dev):
+        st = getattr(lib, fname)(ctypes.c_void_p(A.data_ptr()), n, lda, *extra, ctypes.c_void_p(out.data_ptr()),
+                                 ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.byref(o),
+                                 ctypes.c_void_p(_stream_ptr(dev)))
+    _native.check(st, fname)
+    return out
+
+
+def glynn(A: torch.Tensor, prec="fp64", chunk_log2=0, block=0, grid=0) -> torch.Tensor:
+    """Per(A) by the Gray-ordered BB/FG (Glynn) sum; returns a 0-dim complex128 CUDA tensor."""
+    return _run("perm_glynn", A, (), 1, prec=prec, chunk_log2=chunk_log2, block=block, grid=grid)[0]
+
+
+def ryser(A: torch.Tensor, prec="fp64", chunk_log2=0, block=0, grid=0) -> torch.Tensor:
+    """Per(A) by the Gray-ordered Ryser sum; returns a 0-dim complex128 CUDA tensor."""
+    return _run("perm_ryser", A, (), 1, prec=prec, chunk_log2=chunk_log2, block=block, grid=grid)[0]
+
+
+def _range(fname, A, k_begin, k_end, **opts):
+    out = _run(fname, A, (ctypes.c_uint64(int(k_begin)), ctypes.c_uint64(int(k_end))), 2, **opts)
+    return out  # (hi, lo)
+
+
+def glynn_range(A, k_begin: int, k_end: int, prec="fp64", chunk_log2=0, block=0, grid=0) -> torch.Tensor:
+    """Un-normalised Glynn partial sum over Gray indices [k_begin, k_end): tensor (hi, lo)."""
+    return _range("perm_glynn_range", A, k_begin, k_end, prec=prec, chunk_log2=chunk_log2, block=block, grid=grid)
+
+
+def ryser_range(A, k_begin: int, k_end: int, prec="fp64", chunk_log2=0, block=0, grid=0) -> torch.Tensor:
+    """Un-normalised Ryser partial sum over Gray indices [k_begin, k_end): tensor (hi, lo)."""
+    return _range("perm_ryser_range", A, k_begin, k_end, prec=prec, chunk_log2=chunk_log2, block=block, grid=grid)

@@ -1,0 +1,149 @@
+// Batched permanents of mixed sizes in one persistent, size-bucketed launch.
+//
+// Pipeline (all on the device, so the whole sequence can be captured in one
+// CUDA graph):
+//   1. batch_plan_kernel   one block: validates n, buckets the items by n
+//                          (largest first), cuts every item's Gray range into
+//                          work units of 32 lanes x 2^l terms and prefix-sums the
+//                          unit counts and the per-item column storage.
+//   2. batch_prep_kernel   per item: rows scaled by powers of two, columns
+//                          stored contiguously (column-major), and for Glynn the
+//                          doubled step columns.
+//   3. batch_walk_kernel   persistent: each warp claims the next unit with one
+//                          atomicAdd (bounded by the unit count, no waiting),
+//                          runs the same per-lane Gray walk as the single
+//                          permanent kernel (dispatching on n), and writes the
+//                          unit's double-double partial sum.
+//   4. batch_reduce_kernel per item: its units' partials in unit order
+//                          (deterministic), scaling, and the probability
+//                          epilogue |Per|^2 * scale (Eq. (1) with scale =
+//                          1/(prod s_i! prod t_j!)).
+#pragma once
+#include "common.cuh"
+
+namespace permk {
+
+constexpr int BATCH_MAX_N = 32;
+constexpr int BATCH_PLAN_THREADS = 1024;
+
+__host__ __device__ inline int batch_M(int n, int kind) { return kind == KIND_GLYNN ? n - 1 : n; }
+
+// log2 of the Gray indices per lane in one work unit of an item with 2^M terms
+__host__ __device__ inline int batch_lane_log2(int M, int unit_log2) {
+  int l = M - 5;
+  if (l < 0) l = 0;
+  if (l > unit_log2) l = unit_log2;
+  return l;
+}
+
+__host__ __device__ inline long long batch_units(int M, int unit_log2) {
+  const long long per_unit = 32ll << batch_lane_log2(M, unit_log2);
+  const long long terms = 1ll << M;
+  return (terms + per_unit - 1) / per_unit;
+}
+
+__host__ __device__ inline long long batch_prep_elems(int n, int kind) {
+  return (long long)n * n * (kind == KIND_GLYNN ? 2 : 1);
+}
+
+struct BatchArgs {
+  const double2* packed;   // all matrices, row-major, item i at packed + offsets[i], lda = n_i
+  const long long* offsets;
+  const int* ns;
+  int count;
+  int kind;
+  int unit_log2;
+  int chunk_log2;
+  double neg_zero;
+  // workspace
+  unsigned long long* cursor;
+  int* status;
+  long long* total_units;
+  int* order;            // sorted position -> item
+  int* pos;              // item -> sorted position
+  long long* unit_start; // [count + 1], by sorted position
+  long long* prep_off;   // [count], by item
+  int* scale_exp;        // [count]
+  double* partials;      // 4 doubles per unit
+  double2* prep;
+  long long units_cap;
+  long long prep_cap;
+  // outputs
+  const double* scale;   // nullable
+  double2* out;
+  double* prob;          // nullable
+};
+
+enum { BATCH_OK = 0, BATCH_BAD_N = 1, BATCH_NO_ROOM = 2 };
+
+template <int PREC, int TUNE>
+__device__ __forceinline__ void batch_walk_n(int n, const double2* Acol, const double2* Step, bool glynn, uint64_t kb,
+                                             uint64_t ke, uint64_t CH, double nz, double& ar, double& ai, double& cr,
+                                             double& ci) {
+  switch (n) {
+#define PERM_BCASE(N)                                                                              \
+  case N:                                                                                          \
+    walk_range<N, PREC, TUNE, true>(Acol, Step, N, glynn, kb, ke, CH, nz, ar, ai, cr, ci);        \
+    break;
+    PERM_BCASE(1) PERM_BCASE(2) PERM_BCASE(3) PERM_BCASE(4) PERM_BCASE(5) PERM_BCASE(6) PERM_BCASE(7)
+    PERM_BCASE(8) PERM_BCASE(9) PERM_BCASE(10) PERM_BCASE(11) PERM_BCASE(12) PERM_BCASE(13) PERM_BCASE(14)
+    PERM_BCASE(15) PERM_BCASE(16) PERM_BCASE(17) PERM_BCASE(18) PERM_BCASE(19) PERM_BCASE(20) PERM_BCASE(21)
+    PERM_BCASE(22) PERM_BCASE(23) PERM_BCASE(24) PERM_BCASE(25) PERM_BCASE(26) PERM_BCASE(27) PERM_BCASE(28)
+    PERM_BCASE(29) PERM_BCASE(30) PERM_BCASE(31) PERM_BCASE(32)
+#undef PERM_BCASE
+    default:
+      break;
+  }
+}
+
+template <int PREC, int TUNE>
+__global__ void __launch_bounds__(256, 1) batch_walk_kernel(BatchArgs a) {
+  if (*a.status != BATCH_OK) return;
+  const int lane = threadIdx.x & 31;
+  const long long total = *a.total_units;
+  const uint64_t CH = 1ull << a.chunk_log2;
+  const bool glynn = (a.kind == KIND_GLYNN);
+  const double nz = a.neg_zero;
+  for (;;) {
+    long long u = 0;
+    if (lane == 0) u = (long long)atomicAdd(a.cursor, 1ull);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= total) break;
+    int lo = 0, hi = a.count - 1;  // largest sorted position with unit_start <= u
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.unit_start[mid] <= u) lo = mid;
+      else hi = mid - 1;
+    }
+    const int item = a.order[lo];
+    const int n = a.ns[item];
+    const int M = batch_M(n, a.kind);
+    const int ll = batch_lane_log2(M, a.unit_log2);
+    const long long j = u - a.unit_start[lo];
+    const uint64_t terms = 1ull << M;
+    const uint64_t k0 = ((uint64_t)j * 32ull + (uint64_t)lane) << ll;
+    const uint64_t kb = k0 < terms ? k0 : terms;
+    const uint64_t ke = (k0 + (1ull << ll)) < terms ? k0 + (1ull << ll) : terms;
+    const double2* Acol = a.prep + a.prep_off[item];
+    const double2* Step = glynn ? Acol + n * n : Acol;
+    double ar = 0.0, ai = 0.0, cr = 0.0, ci = 0.0;
+    batch_walk_n<PREC, TUNE>(n, Acol, Step, glynn, kb, ke, CH, nz, ar, ai, cr, ci);
+    dd sr, si;
+    acc_to_dd<PREC>(ar, ai, cr, ci, sr, si);
+    warp_sum_dd(sr, si);
+    if (lane == 0) {
+      double* p = a.partials + 4 * (size_t)u;
+      p[0] = sr.hi;
+      p[1] = sr.lo;
+      p[2] = si.hi;
+      p[3] = si.lo;
+    }
+  }
+}
+
+template <int PREC>
+int launch_batch_walk(const BatchArgs& a, int grid, int block, cudaStream_t s);
+template <int PREC>
+int batch_walk_blocks_per_sm(int block, int* out);
+
+}  // namespace permk

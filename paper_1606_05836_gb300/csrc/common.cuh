@@ -1,0 +1,270 @@
+// Device helpers shared by the permanent kernels: integer-pipe sign handling,
+// double-double sums, FP64<->FP32 conversions on bit patterns, the per-term
+// product and the per-thread Gray-code walk.
+//
+// GB300 FP64 runs at 2 lanes/clk/SM (0.5 per SM sub-partition), ~60x below
+// FP32, so everything that is not the method's FP64 arithmetic is moved to the
+// integer pipe: term signs and update signs are XORs of sign bits, magnitude
+// ordering for compensated sums is an integer compare, and FP64<->FP32
+// conversions of the FP32-product rung are done on the bit patterns.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace permk {
+
+enum { KIND_GLYNN = 0, KIND_RYSER = 1 };
+
+// ---------------------------------------------------------------------------
+// small helpers (integer-pipe sign handling, double-double)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double xor_sign(double x, unsigned long long mask) {
+  return __longlong_as_double(__double_as_longlong(x) ^ mask);
+}
+
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// s + x = s' + e exactly (Fast2Sum with the larger magnitude first, chosen by an
+// integer compare of the bit patterns); e is accumulated into c.
+__device__ __forceinline__ void fast2sum_acc(double& s, double& c, double x) {
+  const bool s_big = abs_bits(s) >= abs_bits(x);
+  const double big = s_big ? s : x;
+  const double small = s_big ? x : s;
+  const double t = s + x;
+  const double e = small - (t - big);
+  c += e;
+  s = t;
+}
+
+struct dd {
+  double hi, lo;
+};
+
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  double s = a.hi + b.hi;
+  double bb = s - a.hi;
+  double e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  double h = s + e;
+  double l = e - (h - s);
+  return dd{h, l};
+}
+
+// FP64 -> FP32 on the integer pipe: round-half-up of the 52-bit mantissa,
+// values below 2^-126 flush to zero, overflow gives infinity.
+__device__ __forceinline__ float f64_to_f32_int(double x) {
+  const unsigned lo = (unsigned)__double2loint(x);
+  const unsigned hi = (unsigned)__double2hiint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  const unsigned mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  unsigned bits = ((unsigned)(e - 896) << 23) + mant + ((lo >> 28) & 1u);
+  bits = (e > 896) ? bits : 0u;
+  bits = (e < 1151) ? bits : 0x7F800000u;
+  return __uint_as_float(sign | bits);
+}
+
+// FP32 -> FP64 on the integer pipe (exact for normal numbers; FP32 subnormals -> 0).
+__device__ __forceinline__ double f32_to_f64_int(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u;
+  const unsigned e = (u >> 23) & 0xFFu;
+  const unsigned m = u & 0x7FFFFFu;
+  unsigned hi = sign | ((e + 896u) << 20) | (m >> 3);
+  unsigned lo = m << 29;
+  hi = (e == 0u) ? sign : hi;
+  lo = (e == 0u) ? 0u : lo;
+  hi = (e == 255u) ? (sign | 0x7FF00000u | (m ? 0x80000u : 0u)) : hi;
+  lo = (e == 255u) ? 0u : lo;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ double pow2_double(int s) {
+  // 2^s for s in [-1022, 1023]
+  return __longlong_as_double((long long)(s + 1023) << 52);
+}
+
+// ---------------------------------------------------------------------------
+// per-term work
+// ---------------------------------------------------------------------------
+
+// TUNE bit 0: Gray update as DFMA(+-1, col, v) instead of DADD with an XOR-ed sign.
+// TUNE bit 1: the products' multiplies as DFMA with a -0.0 addend instead of DMUL.
+template <int TUNE>
+__device__ __forceinline__ double dmul(double x, double y, double nz) {
+  if (TUNE & 2) return fma(x, y, nz);
+  return x * y;
+}
+
+// (pr, pi) <- (pr, pi) * (vr, vi)
+template <int TUNE>
+__device__ __forceinline__ void cmul_inplace(double& pr, double& pi, double vr, double vi, double nz) {
+  const double t = dmul<TUNE>(pi, vi, nz);
+  const double u = dmul<TUNE>(pi, vr, nz);
+  const double nr = fma(pr, vr, -t);
+  const double ni = fma(pr, vi, u);
+  pr = nr;
+  pi = ni;
+}
+
+// R0: acc += sign * prod_i v_i, the last multiply fused into the accumulation.
+template <int N, int TUNE>
+__device__ __forceinline__ void term_r0(const double (&vr)[N], const double (&vi)[N], unsigned long long smask,
+                                        double& ar, double& ai, double nz) {
+  if (N == 1) {
+    ar += xor_sign(vr[0], smask);
+    ai += xor_sign(vi[0], smask);
+    return;
+  }
+  double pr = vr[0], pi = vi[0];
+#pragma unroll
+  for (int i = 1; i < N - 1; i++) cmul_inplace<TUNE>(pr, pi, vr[i], vi[i], nz);
+  pr = xor_sign(pr, smask);
+  pi = xor_sign(pi, smask);
+  ar = fma(pr, vr[N - 1], ar);
+  ar = fma(-pi, vi[N - 1], ar);
+  ai = fma(pr, vi[N - 1], ai);
+  ai = fma(pi, vr[N - 1], ai);
+}
+
+// full FP64 product (R1)
+template <int N, int TUNE>
+__device__ __forceinline__ void prod_f64(const double (&vr)[N], const double (&vi)[N], double& pr, double& pi,
+                                         double nz) {
+  pr = vr[0];
+  pi = vi[0];
+#pragma unroll
+  for (int i = 1; i < N; i++) cmul_inplace<TUNE>(pr, pi, vr[i], vi[i], nz);
+}
+
+// FP32 product of the FP64 row sums (R2); conversions on the integer pipe.
+template <int N>
+__device__ __forceinline__ void prod_f32(const double (&vr)[N], const double (&vi)[N], double& pr, double& pi) {
+  float qr = f64_to_f32_int(vr[0]);
+  float qi = f64_to_f32_int(vi[0]);
+#pragma unroll
+  for (int i = 1; i < N; i++) {
+    const float xr = f64_to_f32_int(vr[i]);
+    const float xi = f64_to_f32_int(vi[i]);
+    const float nr = fmaf(qr, xr, -qi * xi);
+    const float ni = fmaf(qr, xi, qi * xr);
+    qr = nr;
+    qi = ni;
+  }
+  pr = f32_to_f64_int(qr);
+  pi = f32_to_f64_int(qi);
+}
+
+// ---------------------------------------------------------------------------
+// one thread's Gray walk over [kb, ke) (steps a2-a5)
+// ---------------------------------------------------------------------------
+
+template <bool GLOBAL>
+__device__ __forceinline__ double2 ldcol(const double2* p) {
+  if (GLOBAL) return __ldg(p);
+  return *p;
+}
+
+// Walks Gray indices [kb, ke): at every chunk start (every CH steps from kb) the
+// row sums are recomputed exactly from the columns Acol (v_i = sum_j coef_j a_ij,
+// Glynn: coef_0 = +1 and coef_{b+1} = -1 iff bit b of g(k) is set; Ryser:
+// coef_b = [bit b of g(k)]); every other step adds +-Step[b], b = ctz(k).
+// Columns are `stride` complex numbers apart.  GLOBAL selects read-only global
+// loads instead of shared-memory loads.
+template <int N, int PREC, int TUNE, bool GLOBAL>
+__device__ __forceinline__ void walk_range(const double2* __restrict__ Acol, const double2* __restrict__ Step,
+                                           int stride, bool glynn, uint64_t kb, uint64_t ke, uint64_t CH, double nz,
+                                           double& ar, double& ai, double& cr, double& ci) {
+  // Glynn: a set Gray bit means delta = -1 (subtract 2a when it turns on);
+  // Ryser: a set bit means the column is in S (add a when it turns on).
+  const unsigned long long on_mask = glynn ? 0x8000000000000000ull : 0ull;
+  for (uint64_t c0 = kb; c0 < ke; c0 += CH) {
+    const uint64_t c1 = (ke - c0 > CH) ? c0 + CH : ke;
+    uint64_t g = c0 ^ (c0 >> 1);
+    double vr[N], vi[N];
+    // exact row sums at the chunk start: v_i = sum_j coef_j a_ij
+#pragma unroll
+    for (int i = 0; i < N; i++) { vr[i] = 0.0; vi[i] = 0.0; }
+#pragma unroll 1
+    for (int j = 0; j < N; j++) {
+      double coef;
+      if (glynn) coef = (j == 0) ? 1.0 : (((g >> (j - 1)) & 1ull) ? -1.0 : 1.0);
+      else coef = ((g >> j) & 1ull) ? 1.0 : 0.0;
+      const double2* col = Acol + j * stride;
+#pragma unroll
+      for (int i = 0; i < N; i++) {
+        const double2 x = ldcol<GLOBAL>(col + i);
+        vr[i] = fma(coef, x.x, vr[i]);
+        vi[i] = fma(coef, x.y, vi[i]);
+      }
+    }
+    uint64_t k = c0;
+#pragma unroll 1
+    while (true) {
+      // term sign (prod delta) = (-1)^popcount(g(k)) = (-1)^(k & 1)
+      const unsigned long long smask = (k & 1ull) << 63;
+      if (PREC == 0) {
+        term_r0<N, TUNE>(vr, vi, smask, ar, ai, nz);
+      } else {
+        double pr, pi;
+        if (PREC == 1) prod_f64<N, TUNE>(vr, vi, pr, pi, nz);
+        else prod_f32<N>(vr, vi, pr, pi);
+        fast2sum_acc(ar, cr, xor_sign(pr, smask));
+        fast2sum_acc(ai, ci, xor_sign(pi, smask));
+      }
+      ++k;
+      if (k >= c1) break;
+      // Gray step: bit b = ctz(k) flips
+      const int b = __ffsll((long long)k) - 1;
+      g ^= 1ull << b;
+      // negative iff (Glynn and the bit turned on) or (Ryser and it turned off)
+      const unsigned long long umask = ((((g >> b) & 1ull) ^ 1ull) << 63) ^ on_mask;
+      const double2* col = Step + b * stride;
+      if (TUNE & 1) {
+        const double sgn = xor_sign(1.0, umask);
+#pragma unroll
+        for (int i = 0; i < N; i++) {
+          const double2 x = ldcol<GLOBAL>(col + i);
+          vr[i] = fma(sgn, x.x, vr[i]);
+          vi[i] = fma(sgn, x.y, vi[i]);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < N; i++) {
+          const double2 x = ldcol<GLOBAL>(col + i);
+          vr[i] += xor_sign(x.x, umask);
+          vi[i] += xor_sign(x.y, umask);
+        }
+      }
+    }
+  }
+
+}
+
+// Warp butterfly sum of double-double pairs (every lane ends with the same sum).
+__device__ __forceinline__ void warp_sum_dd(dd& sr, dd& si) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    dd orr{__shfl_xor_sync(0xffffffffu, sr.hi, off), __shfl_xor_sync(0xffffffffu, sr.lo, off)};
+    dd oii{__shfl_xor_sync(0xffffffffu, si.hi, off), __shfl_xor_sync(0xffffffffu, si.lo, off)};
+    sr = dd_add(sr, orr);
+    si = dd_add(si, oii);
+  }
+}
+
+// Per-thread (sum, compensation) -> normalised double-double.
+template <int PREC>
+__device__ __forceinline__ void acc_to_dd(double ar, double ai, double cr, double ci, dd& sr, dd& si) {
+  if (PREC != 0) {
+    sr = dd_add(dd{ar, 0.0}, dd{cr, 0.0});
+    si = dd_add(dd{ai, 0.0}, dd{ci, 0.0});
+  } else {
+    sr = dd{ar, 0.0};
+    si = dd{ai, 0.0};
+  }
+}
+
+}  // namespace permk

@@ -1,0 +1,235 @@
+// C ABI of libperm: argument checks, launch planning and dispatch to the
+// templated kernels.  The declarations and their contracts are in include/perm.h.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+
+#include "fwd_kernel.cuh"
+#include "host_util.h"
+#include "perm.h"
+
+namespace {
+
+thread_local int g_last_cuda = 0;
+
+int fail_cuda(cudaError_t e) {
+  g_last_cuda = (int)e;
+  return PERM_ECUDA;
+}
+
+int fail_cuda_int(int e) {
+  g_last_cuda = e;
+  return PERM_ECUDA;
+}
+
+// Instruction-mix override for tuning runs (PERM_TUNE=0..3); -1 = library default.
+int tune_override() {
+  static int cached = -2;
+  if (cached == -2) {
+    const char* s = getenv("PERM_TUNE");
+    cached = (s && *s) ? atoi(s) : -1;
+  }
+  return cached;
+}
+
+int dispatch_launch(int n, const permk::FwdArgs& a, int prec, int tune, int grid, int block, cudaStream_t s) {
+  switch (n) {
+#define PERM_CASE(N) \
+  case N:            \
+    return permk::launch_fwd<N>(a, prec, tune, grid, block, s);
+    PERM_CASE(1) PERM_CASE(2) PERM_CASE(3) PERM_CASE(4) PERM_CASE(5) PERM_CASE(6) PERM_CASE(7) PERM_CASE(8)
+    PERM_CASE(9) PERM_CASE(10) PERM_CASE(11) PERM_CASE(12) PERM_CASE(13) PERM_CASE(14) PERM_CASE(15)
+    PERM_CASE(16) PERM_CASE(17) PERM_CASE(18) PERM_CASE(19) PERM_CASE(20) PERM_CASE(21) PERM_CASE(22)
+    PERM_CASE(23) PERM_CASE(24) PERM_CASE(25) PERM_CASE(26) PERM_CASE(27) PERM_CASE(28) PERM_CASE(29)
+    PERM_CASE(30) PERM_CASE(31) PERM_CASE(32) PERM_CASE(33) PERM_CASE(34) PERM_CASE(35) PERM_CASE(36)
+    PERM_CASE(37) PERM_CASE(38) PERM_CASE(39) PERM_CASE(40) PERM_CASE(41) PERM_CASE(42) PERM_CASE(43)
+    PERM_CASE(44) PERM_CASE(45) PERM_CASE(46) PERM_CASE(47) PERM_CASE(48)
+#undef PERM_CASE
+    default:
+      return (int)cudaErrorInvalidValue;
+  }
+}
+
+int dispatch_occupancy(int n, int prec, int tune, int block, int kind, int* out) {
+  switch (n) {
+#define PERM_CASE(N) \
+  case N:            \
+    return permk::fwd_blocks_per_sm<N>(prec, tune, block, kind, out);
+    PERM_CASE(1) PERM_CASE(2) PERM_CASE(3) PERM_CASE(4) PERM_CASE(5) PERM_CASE(6) PERM_CASE(7) PERM_CASE(8)
+    PERM_CASE(9) PERM_CASE(10) PERM_CASE(11) PERM_CASE(12) PERM_CASE(13) PERM_CASE(14) PERM_CASE(15)
+    PERM_CASE(16) PERM_CASE(17) PERM_CASE(18) PERM_CASE(19) PERM_CASE(20) PERM_CASE(21) PERM_CASE(22)
+    PERM_CASE(23) PERM_CASE(24) PERM_CASE(25) PERM_CASE(26) PERM_CASE(27) PERM_CASE(28) PERM_CASE(29)
+    PERM_CASE(30) PERM_CASE(31) PERM_CASE(32) PERM_CASE(33) PERM_CASE(34) PERM_CASE(35) PERM_CASE(36)
+    PERM_CASE(37) PERM_CASE(38) PERM_CASE(39) PERM_CASE(40) PERM_CASE(41) PERM_CASE(42) PERM_CASE(43)
+    PERM_CASE(44) PERM_CASE(45) PERM_CASE(46) PERM_CASE(47) PERM_CASE(48)
+#undef PERM_CASE
+    default:
+      return (int)cudaErrorInvalidValue;
+  }
+}
+
+struct Plan {
+  int prec, tune, chunk_log2, block, grid;
+  uint64_t per_q, per_r;
+};
+
+int sm_count(int* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail_cuda(e);
+  e = cudaDeviceGetAttribute(out, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return fail_cuda(e);
+  return PERM_OK;
+}
+
+int read_opts(const perm_opts* o, int* prec, int* chunk_log2, int* block, int* grid) {
+  *prec = o ? o->prec : PERM_FP64;
+  *chunk_log2 = (o && o->chunk_log2) ? o->chunk_log2 : 12;
+  *block = (o && o->block) ? o->block : 128;
+  *grid = o ? o->grid : 0;
+  if (*prec < PERM_FP64 || *prec > PERM_FP32P_DD) return PERM_EINVAL;
+  if (*chunk_log2 < 1 || *chunk_log2 > 30) return PERM_EINVAL;
+  if (*block < 32 || *block > 256 || (*block & 31)) return PERM_EINVAL;
+  if (*grid < 0) return PERM_EINVAL;
+  return PERM_OK;
+}
+
+// Full grid for a kernel instance: SMs x resident blocks per SM, so that every
+// SM sub-partition holds the same number of warps (one wave, equal work).
+int full_grid(int n, int kind, int prec, int tune, int block, int* grid) {
+  int sms = 0, bps = 0;
+  int st = sm_count(&sms);
+  if (st) return st;
+  int e = dispatch_occupancy(n, prec, tune, block, kind, &bps);
+  if (e) return fail_cuda_int(e);
+  if (bps < 1) return fail_cuda(cudaErrorInvalidConfiguration);
+  *grid = sms * bps;
+  return PERM_OK;
+}
+
+int plan_fwd(int n, int kind, uint64_t range, const perm_opts* o, Plan* p) {
+  int grid_opt = 0;
+  int st = read_opts(o, &p->prec, &p->chunk_log2, &p->block, &grid_opt);
+  if (st) return st;
+  p->tune = tune_override();
+  if (grid_opt > 0) {
+    p->grid = grid_opt;
+  } else {
+    int g = 0;
+    st = full_grid(n, kind, p->prec, p->tune, p->block, &g);
+    if (st) return st;
+    const uint64_t need = (range + (uint64_t)p->block - 1) / (uint64_t)p->block;
+    p->grid = (uint64_t)g < need ? g : (int)(need > 0 ? need : 1);
+  }
+  const uint64_t P = (uint64_t)p->grid * (uint64_t)p->block;
+  p->per_q = range / P;
+  p->per_r = range % P;
+  return PERM_OK;
+}
+
+size_t workspace_for_grid(int grid) { return 256 + (size_t)grid * 4 * sizeof(double); }
+
+__global__ void set_one_kernel(double2* out) { out[0] = make_double2(1.0, 0.0); }
+
+int run_fwd(const perm_c128* dA, int n, int lda, int kind, uint64_t k_begin, uint64_t k_end, int raw,
+            perm_c128* dOut, void* dWork, size_t workBytes, const perm_opts* opts, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n < 0 || n > PERM_MAX_N) return PERM_ERANGE;
+  if (!dOut || (n > 0 && !dA)) return PERM_EINVAL;
+  if (lda < n) return PERM_EINVAL;
+  if (((uintptr_t)dA & 15u) || ((uintptr_t)dOut & 15u)) return PERM_EINVAL;
+  if (n == 0) {
+    if (raw) return PERM_ERANGE;
+    set_one_kernel<<<1, 1, 0, s>>>((double2*)dOut);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PERM_OK : fail_cuda(e);
+  }
+  const int M = (kind == permk::KIND_GLYNN) ? n - 1 : n;
+  const uint64_t full = 1ull << M;
+  if (k_begin > k_end || k_end > full) return PERM_ERANGE;
+  Plan p;
+  int st = plan_fwd(n, kind, k_end - k_begin, opts, &p);
+  if (st) return st;
+  if (!dWork || ((uintptr_t)dWork & 15u)) return PERM_EINVAL;
+  if (workBytes < workspace_for_grid(p.grid)) return PERM_ENOMEM;
+  permk::FwdArgs a;
+  a.A = (const double2*)dA;
+  a.n = n;
+  a.lda = lda;
+  a.kind = kind;
+  a.chunk_log2 = p.chunk_log2;
+  a.k_begin = k_begin;
+  a.k_end = k_end;
+  a.per_q = p.per_q;
+  a.per_r = p.per_r;
+  a.neg_zero = -0.0;
+  a.ticket = (unsigned*)dWork;
+  a.partials = (double*)((char*)dWork + 256);
+  a.out = (double2*)dOut;
+  a.raw = raw;
+  cudaError_t e = cudaMemsetAsync(dWork, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return fail_cuda(e);
+  int le = dispatch_launch(n, a, p.prec, p.tune, p.grid, p.block, s);
+  if (le) return fail_cuda_int(le);
+  return PERM_OK;
+}
+
+}  // namespace
+
+void permk::record_cuda_error(int err) { g_last_cuda = err; }
+
+extern "C" {
+
+size_t perm_workspace_size(int n, const perm_opts* opts) {
+  if (n < 1 || n > PERM_MAX_N) return workspace_for_grid(1);
+  int prec, chunk, block, grid_opt;
+  if (read_opts(opts, &prec, &chunk, &block, &grid_opt)) return 0;
+  if (grid_opt > 0) return workspace_for_grid(grid_opt);
+  int g0 = 0, g1 = 0;
+  if (full_grid(n, permk::KIND_GLYNN, prec, tune_override(), block, &g0)) return 0;
+  if (full_grid(n, permk::KIND_RYSER, prec, tune_override(), block, &g1)) return 0;
+  return workspace_for_grid(g0 > g1 ? g0 : g1);
+}
+
+int perm_glynn(const perm_c128* dA, int n, int lda, perm_c128* dOut, void* dWork, size_t workBytes,
+               const perm_opts* opts, void* stream) {
+  const uint64_t full = (n >= 1 && n <= PERM_MAX_N) ? (1ull << (n - 1)) : 0;
+  return run_fwd(dA, n, lda, permk::KIND_GLYNN, 0, full, 0, dOut, dWork, workBytes, opts, stream);
+}
+
+int perm_ryser(const perm_c128* dA, int n, int lda, perm_c128* dOut, void* dWork, size_t workBytes,
+               const perm_opts* opts, void* stream) {
+  const uint64_t full = (n >= 1 && n <= PERM_MAX_N) ? (1ull << n) : 0;
+  return run_fwd(dA, n, lda, permk::KIND_RYSER, 0, full, 0, dOut, dWork, workBytes, opts, stream);
+}
+
+int perm_glynn_range(const perm_c128* dA, int n, int lda, uint64_t k_begin, uint64_t k_end, perm_c128* dOut,
+                     void* dWork, size_t workBytes, const perm_opts* opts, void* stream) {
+  if (n < 1) return PERM_ERANGE;
+  return run_fwd(dA, n, lda, permk::KIND_GLYNN, k_begin, k_end, 1, dOut, dWork, workBytes, opts, stream);
+}
+
+int perm_ryser_range(const perm_c128* dA, int n, int lda, uint64_t k_begin, uint64_t k_end, perm_c128* dOut,
+                     void* dWork, size_t workBytes, const perm_opts* opts, void* stream) {
+  if (n < 1) return PERM_ERANGE;
+  return run_fwd(dA, n, lda, permk::KIND_RYSER, k_begin, k_end, 1, dOut, dWork, workBytes, opts, stream);
+}
+
+const char* perm_strerror(int status) {
+  switch (status) {
+    case PERM_OK: return "ok";
+    case PERM_EINVAL: return "invalid argument";
+    case PERM_ERANGE: return "size or index range out of bounds";
+    case PERM_ENOMEM: return "workspace too small";
+    case PERM_ECUDA: return "CUDA runtime error";
+    case PERM_ENONFINITE: return "non-finite value";
+    case PERM_ETIMEOUT: return "bounded wait timed out";
+    default: return "unknown status";
+  }
+}
+
+int perm_last_cuda_error(void) { return g_last_cuda; }
+
+int perm_version(void) { return PERM_ABI_VERSION; }
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+"""The C-ABI library builds, loads and exports every symbol include/perm.h declares.
+
+No compute call is made here (no GPU on this host); only host-side helpers
+(perm_strerror, perm_version) are called.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for f in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not f.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b([A-Za-z_][A-Za-z0-9_]*)\s*\(", text):
+            name = m.group(1)
+            if name.startswith("perm_") and not name.startswith("perm_c128"):
+                names.append(name)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1606_05836_gb300 import build, _native
+    build.build()
+    return _native.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "perm_glynn" in names and "perm_ryser" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_python_binding_lists_the_same_symbols():
+    from paper_1606_05836_gb300 import _native
+    assert sorted(_native.EXPORTS) == declared_functions()
+
+
+def test_host_helpers(lib):
+    assert lib.perm_version() == 1
+    assert lib.perm_strerror(0) == b"ok"
+    assert lib.perm_strerror(-2).startswith(b"size")
+    assert lib.perm_strerror(12345) == b"unknown status"
+
+
+def test_argument_errors_before_any_launch(lib):
+    """Host-detectable errors return before touching the device."""
+    from paper_1606_05836_gb300._native import Opts
+    o = Opts(0, 0, 0, 0, 0)
+    # n out of range
+    assert lib.perm_glynn(None, 49, 49, None, None, 0, ctypes.byref(o), None) == -2
+    assert lib.perm_ryser(None, -1, 0, None, None, 0, ctypes.byref(o), None) == -2
+    # null output
+    assert lib.perm_glynn(ctypes.c_void_p(16), 4, 4, None, ctypes.c_void_p(16), 1 << 20, ctypes.byref(o), None) == -1
+    # lda < n
+    assert lib.perm_glynn(ctypes.c_void_p(16), 4, 3, ctypes.c_void_p(32), ctypes.c_void_p(64), 1 << 20,
+                          ctypes.byref(o), None) == -1
+    # misaligned matrix pointer
+    assert lib.perm_ryser(ctypes.c_void_p(8), 4, 4, ctypes.c_void_p(32), ctypes.c_void_p(64), 1 << 20,
+                          ctypes.byref(o), None) == -1
+    # bad options
+    bad = Opts(7, 0, 0, 0, 0)
+    assert lib.perm_glynn(ctypes.c_void_p(16), 4, 4, ctypes.c_void_p(32), ctypes.c_void_p(64), 1 << 20,
+                          ctypes.byref(bad), None) == -1
+    bad = Opts(0, 0, 100, 0, 0)
+    assert lib.perm_glynn(ctypes.c_void_p(16), 4, 4, ctypes.c_void_p(32), ctypes.c_void_p(64), 1 << 20,
+                          ctypes.byref(bad), None) == -1
+    # range beyond 2^(n-1) for Glynn
+    assert lib.perm_glynn_range(ctypes.c_void_p(16), 4, 4, 0, 9, ctypes.c_void_p(32), ctypes.c_void_p(64), 1 << 20,
+                                ctypes.byref(o), None) == -2
+    assert lib.perm_ryser_range(ctypes.c_void_p(16), 4, 4, 5, 3, ctypes.c_void_p(32), ctypes.c_void_p(64), 1 << 20,
+                                ctypes.byref(o), None) == -2

@@ -1,0 +1,194 @@
+"""GPU parity of the single-permanent path (perm_glynn / perm_ryser / *_range)
+against the CPU oracle, through the C ABI.
+
+Bar: relative error <= 1e-10 in FP64 against the quad (or exact) oracle; exact
+equality where FP64 arithmetic is exact (integer matrices with small entries).
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+from conftest import read_tsv
+from gpu_util import REL_TOL, pair, rel, row_scale, to_dev, val
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pg():
+    import paper_1606_05836_gb300 as pg
+    from paper_1606_05836_gb300 import build
+    build.build()
+    pg.library()
+    return pg
+
+
+# ---------------------------------------------------------------- config 1
+def test_config1_haar_block_n20(pg):
+    A = S.haar_block(20, 400, 0)
+    want = oracle.glynn(A)
+    dA = to_dev(A)
+    assert rel(val(pg.glynn(dA)), want) < REL_TOL
+    assert rel(val(pg.ryser(dA)), want) < REL_TOL
+
+
+def test_config1_fixed_checks_exact(pg):
+    ex = {r["name"]: r for r in read_tsv("worked_examples.tsv")}
+    ones = to_dev(S.all_r(12, 1.0))
+    jmi = to_dev(S.ones_minus_identity(12))
+    for f in (pg.glynn, pg.ryser):
+        assert val(f(ones)) == complex(float(ex["ones"]["value_re"]), 0.0)
+        assert val(f(jmi)) == complex(float(ex["ones_minus_identity"]["value_re"]), 0.0)
+
+
+# ------------------------------------------------------- small sizes, all rungs
+@pytest.mark.parametrize("n", list(range(1, 17)))
+def test_gaussian_small_all_rungs(pg, n):
+    A = S.gaussian(n, 100 + n, 1.0)
+    want = oracle.perm_def(A) if n <= 9 else oracle.ryser(A)
+    dA = to_dev(A)
+    # FP32-product rung: its own (stated) error, far above FP64's; Ryser's
+    # 2^n-term cancellation amplifies it more than Glynn's.
+    r2_tol = {"glynn": 1e-4, "ryser": 1e-2}
+    for f in (pg.glynn, pg.ryser):
+        for prec, tol in (("fp64", REL_TOL), ("fp64_dd", REL_TOL), ("fp32p_dd", r2_tol[f.__name__])):
+            got = val(f(dA, prec=prec))
+            assert rel(got, want) < tol, (f.__name__, prec, got, want.hi)
+
+
+def test_n0_is_one(pg):
+    import torch
+    A = torch.zeros((0, 0), dtype=torch.complex128, device="cuda")
+    assert val(pg.glynn(A)) == 1 and val(pg.ryser(A)) == 1
+
+
+def test_strided_lda(pg):
+    big = S.gaussian(24, 7, 1.0)
+    A = big[:13, :13]
+    want = oracle.ryser(A)
+    dbig = to_dev(big)
+    sub = dbig[:13, :13]  # lda = 24
+    assert sub.stride(0) == 24
+    assert rel(val(pg.glynn(sub)), want) < REL_TOL
+    assert rel(val(pg.ryser(sub)), want) < REL_TOL
+
+
+# ------------------------------------------------- launch shapes, ragged tails
+@pytest.mark.parametrize("opts", [
+    dict(chunk_log2=1), dict(chunk_log2=3, block=96), dict(chunk_log2=5, grid=7, block=32),
+    dict(chunk_log2=30), dict(grid=1000, block=256), dict(grid=3, block=64, chunk_log2=2),
+])
+def test_launch_shapes_same_result(pg, opts):
+    A = S.gaussian(18, 55, 1.0)
+    want = oracle.glynn(A)
+    dA = to_dev(A)
+    for prec in ("fp64", "fp64_dd"):
+        assert rel(val(pg.glynn(dA, prec=prec, **opts)), want) < REL_TOL
+        assert rel(val(pg.ryser(dA, prec=prec, **opts)), want) < REL_TOL
+
+
+def test_deterministic_for_fixed_launch(pg):
+    dA = to_dev(S.gaussian(22, 9))
+    a, b = val(pg.glynn(dA)), val(pg.glynn(dA))
+    assert a == b
+
+
+# ------------------------------------------------------- Gray-range partials
+@pytest.mark.parametrize("n,kb,ke", [(20, 0, 1 << 19), (20, 12345, 12345 + 70001), (20, (1 << 19) - 33, 1 << 19),
+                                     (17, 5, 5), (17, 7, 8)])
+def test_glynn_range_vs_oracle(pg, n, kb, ke):
+    A = S.gaussian(n, 200 + n)
+    want = oracle.glynn_range(A, kb, ke, gray=True)
+    hi, lo = pair(pg.glynn_range(to_dev(A), kb, ke))
+    scale = row_scale(A) * math.sqrt(max(ke - kb, 1))
+    assert abs((hi - want.hi) + (lo - want.lo)) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("n,kb,ke", [(19, 1, 1 << 19), (19, 4097, 4097 + 65536), (19, (1 << 19) - 1, 1 << 19)])
+def test_ryser_range_vs_oracle(pg, n, kb, ke):
+    A = S.gaussian(n, 300 + n)
+    want = oracle.ryser_range(A, kb, ke, gray=True)
+    hi, lo = pair(pg.ryser_range(to_dev(A), kb, ke))
+    scale = row_scale(A) * math.sqrt(max(ke - kb, 1))
+    assert abs((hi - want.hi) + (lo - want.lo)) <= 1e-12 * scale
+
+
+def test_sampled_range_n40(pg):
+    """Full-size n = 40: a sampled 2^15-term Gray range at an unaligned offset."""
+    n = 40
+    A = S.gaussian(n, 4000)
+    kb = 387654321123  # < 2^39
+    ke = kb + (1 << 15)
+    want = oracle.glynn_range(A, kb, ke, gray=True)
+    hi, lo = pair(pg.glynn_range(to_dev(A), kb, ke))
+    scale = row_scale(A) * math.sqrt(ke - kb)
+    assert abs((hi - want.hi) + (lo - want.lo)) <= 1e-12 * scale
+
+
+def test_paper_diag_1pi_n45_range(pg):
+    """The paper's 45x45 diag(1+i) run: every Glynn term is (1+i)^45."""
+    n = 45
+    A = S.diagonal([1 + 1j] * n)
+    want = (1 + 1j) ** 45
+    dA = to_dev(A)
+    for kb, ke in [(0, 1 << 20), ((1 << 44) - 12345, 1 << 44)]:
+        hi, lo = pair(pg.glynn_range(dA, kb, ke))
+        assert hi + lo == (ke - kb) * want
+
+
+# ---------------------------------------------------------- large-n properties
+def test_block_diagonal_n32(pg):
+    B1, B2 = S.gaussian(16, 501), S.gaussian(16, 502)
+    A = np.zeros((32, 32), dtype=np.complex128)
+    A[:16, :16], A[16:, 16:] = B1, B2
+    P, Q = S.random_permutations(32, 503)
+    A = A[P][:, Q]
+    want = oracle.ryser(B1).hi * oracle.glynn(B2).hi
+    assert rel(val(pg.glynn(to_dev(A))), want) < REL_TOL
+
+
+def test_rank_one_n32(pg):
+    A, u, v = S.rank_one(32, 601)
+    want = math.factorial(32) * np.prod(u) * np.prod(v)
+    assert rel(val(pg.glynn(to_dev(A))), want) < REL_TOL
+
+
+def test_invariances_n30(pg):
+    A = S.gaussian(30, 701)
+    dA = to_dev(A)
+    p = val(pg.glynn(dA))
+    P, Q = S.random_permutations(30, 702)
+    assert rel(val(pg.glynn(to_dev(A.T))), p) < REL_TOL
+    assert rel(val(pg.glynn(to_dev(A[P][:, Q]))), p) < REL_TOL
+    # Ryser's FP64 error is far larger than Glynn's: the paper's random-matrix
+    # comparisons (Supp. tables of Ryser vs BB/FG results) differ by up to 5e-6
+    # at n = 31-40.
+    assert rel(val(pg.ryser(dA)), p) < 1e-5
+    assert rel(val(pg.ryser(dA, prec="fp64_dd")), p) < 1e-5
+
+
+# ---------------------------------------------- paper's Ryser-vs-BB/FG precision
+def test_precision_gap_allones_matches_paper(pg):
+    """FP64 on all-ones: BB/FG stays accurate while Ryser's error reaches O(1)
+    near n = 30-32; same orders of magnitude as the paper's tables."""
+    paper = {int(r["n"]): (float(r["bbfg_relerr"]), float(r["ryser_relerr"])) for r in
+             read_tsv("precision_allones.tsv")}
+    results = {}
+    for n in (20, 24, 28, 30, 32):
+        dA = to_dev(S.all_r(n, 1.0))
+        exact = math.factorial(n)
+        eg = abs(Fraction(val(pg.glynn(dA)).real) - exact) / exact
+        er = abs(Fraction(val(pg.ryser(dA)).real) - exact) / exact
+        results[n] = (float(eg), float(er))
+    for n, (eg, er) in results.items():
+        pg_, pr_ = paper[n]
+        assert eg <= 100 * pg_ + 1e-15, (n, eg, pg_)
+        assert pr_ / 100 <= er <= 100 * pr_ + 1e-6, (n, er, pr_)
+    # the gap: Ryser 10^5+ times worse once n >= 28
+    for n in (28, 30, 32):
+        eg, er = results[n]
+        assert er > 1e5 * max(eg, 1e-16)
