@@ -125,6 +125,32 @@ int perm_batched(const perm_c128* dPacked, const int64_t* dOffsets, const int32_
                  int method, const double* dScale, perm_c128* dOut, double* dProb, void* dWork, size_t workBytes,
                  const perm_opts* opts, void* stream);
 
+/* --- without caller memory ----------------------------------------------- */
+
+/* perm_glynn without a workspace argument: the same computation and kernel as
+ * perm_glynn, but the kernel's scratch (the last-block ticket and the per-block
+ * partial sums) lives in a fixed array inside the library.  The paper has no
+ * counterpart; this exists for callers that cannot allocate device memory —
+ * for instance code embedded in a host application that owns and budgets all
+ * GPU memory, or a latency-critical path that must not call cudaMalloc because
+ * it can synchronise the device and stall other streams.
+ *
+ * - The array is PERM_NOALLOC_SCRATCH_BYTES of device memory per GPU that loads
+ *   the library, held until the process exits; nothing is allocated or freed per
+ *   call.  A launch needing more than PERM_NOALLOC_MAX_BLOCKS blocks (an explicit
+ *   opts->grid above it) is rejected with PERM_ENOMEM.
+ * - The first call on each device looks the array's device address up
+ *   (cudaGetSymbolAddress) with that device current; make that first call before
+ *   any stream capture begins.
+ * - All calls share the one array, which keeps the previous call's contents
+ *   (the ticket is cleared on the stream before each launch).  Calls whose
+ *   kernels overlap on the GPU — different streams or host threads without
+ *   ordering between them — race on it: order them on one stream.
+ * Arguments and results are as for perm_glynn. */
+#define PERM_NOALLOC_MAX_BLOCKS 4096
+#define PERM_NOALLOC_SCRATCH_BYTES (256 + 32 * PERM_NOALLOC_MAX_BLOCKS)
+int perm_glynn_noalloc(const perm_c128* dA, int n, int lda, perm_c128* dOut, const perm_opts* opts, void* stream);
+
 /* --- diagnostics ----------------------------------------------------------- */
 
 const char* perm_strerror(int status);

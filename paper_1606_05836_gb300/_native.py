@@ -24,6 +24,7 @@ EXPORTS = (
     "perm_ryser_range",
     "perm_batched_workspace_size",
     "perm_batched",
+    "perm_glynn_noalloc",
     "perm_strerror",
     "perm_last_cuda_error",
     "perm_version",
@@ -72,6 +73,8 @@ def load(path: str | None = None):
     lib.perm_batched_workspace_size.restype = sz
     lib.perm_batched.argtypes = [vp, vp, vp, i32p, i32, i32, vp, vp, vp, vp, sz, op, vp]
     lib.perm_batched.restype = i32
+    lib.perm_glynn_noalloc.argtypes = [vp, i32, i32, vp, op, vp]
+    lib.perm_glynn_noalloc.restype = i32
     lib.perm_strerror.argtypes = [i32]
     lib.perm_strerror.restype = ctypes.c_char_p
     lib.perm_last_cuda_error.argtypes = []

@@ -4,6 +4,8 @@
 #include <stdint.h>
 #include <stdlib.h>
 
+#include <mutex>
+
 #include "fwd_kernel.cuh"
 #include "host_util.h"
 #include "perm.h"
@@ -233,3 +235,63 @@ int perm_last_cuda_error(void) { return g_last_cuda; }
 int perm_version(void) { return PERM_ABI_VERSION; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// perm_glynn_noalloc: the Glynn kernel with its scratch in a fixed device array
+// ---------------------------------------------------------------------------
+//
+// Scratch of the single-permanent kernel = a 256-byte header (the last-block
+// ticket) + 32 bytes of double-double partial sums per block.  Here it lives in
+// one file-scope device array instead of a caller workspace, for callers that
+// may not allocate device memory themselves.  Every GPU that loads this library
+// holds the array (PERM_NOALLOC_SCRATCH_BYTES) until the process exits.
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[PERM_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device (with that device current) and cached.
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail_cuda(e);
+  if (dev < 0 || dev >= kMaxDevices) return PERM_EINVAL;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return fail_cuda(e);
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return PERM_OK;
+}
+
+}  // namespace
+
+extern "C" int perm_glynn_noalloc(const perm_c128* dA, int n, int lda, perm_c128* dOut, const perm_opts* opts,
+                                  void* stream) {
+  if (n < 0 || n > PERM_MAX_N) return PERM_ERANGE;
+  if (!dOut || (n > 0 && !dA)) return PERM_EINVAL;
+  void* scratch = nullptr;
+  int st = noalloc_scratch(&scratch);
+  if (st) return st;
+  if (n >= 1) {
+    // the launch this call would make must fit the fixed partial-sum array
+    Plan p;
+    st = plan_fwd(n, permk::KIND_GLYNN, 1ull << (n - 1), opts, &p);
+    if (st) return st;
+    if (workspace_for_grid(p.grid) > (size_t)PERM_NOALLOC_SCRATCH_BYTES) return PERM_ENOMEM;
+  }
+  // run_fwd zeroes the ticket (the only scratch that must start at zero) with
+  // cudaMemsetAsync before the launch; partials are written before they are read.
+  const uint64_t full = (n >= 1) ? (1ull << (n - 1)) : 0;
+  return run_fwd(dA, n, lda, permk::KIND_GLYNN, 0, full, 0, dOut, scratch, (size_t)PERM_NOALLOC_SCRATCH_BYTES, opts,
+                 stream);
+}
