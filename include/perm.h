@@ -125,6 +125,46 @@ int perm_batched(const perm_c128* dPacked, const int64_t* dOffsets, const int32_
                  int method, const double* dScale, perm_c128* dOut, double* dProb, void* dWork, size_t workBytes,
                  const perm_opts* opts, void* stream);
 
+/* --- one output probability ------------------------------------------------ */
+
+/* Eq. (1) of arXiv 1606.05836 for one input pattern S and output pattern T:
+ *     Pr[S -> T] = |Per(U_ST)|^2 / (s_1! ... s_m! t_1! ... t_m!).
+ * dU:  the m x m interferometer unitary (device, row-major, ldu >= m); U[i][j] is
+ *      the amplitude from input mode i to output mode j.
+ * hS, hT: host occupation vectors of length m with equal sums n <= PERM_MAX_N.
+ *      Row r of U_ST is input mode i repeated s_i times (ascending i), column c is
+ *      output mode j repeated t_j times (the paper defers U_ST's construction to
+ *      Aaronson-Arkhipov; this orientation is the one stated here).
+ * hProb: host result.  hPerm: nullable host Per(U_ST).
+ * dWork: 256-byte-aligned workspace of prob_sample_workspace_size(n) bytes.
+ * U_ST is gathered on the device and Per(U_ST) is the Glynn kernel's; the call
+ * synchronises `stream` and returns with *hProb written. */
+size_t prob_sample_workspace_size(int n, const perm_opts* opts);
+int prob_sample(const perm_c128* dU, int m, int ldu, const int32_t* hS, const int32_t* hT, double* hProb,
+                perm_c128* hPerm, void* dWork, size_t workBytes, const perm_opts* opts, void* stream);
+
+/* --- adjoint ---------------------------------------------------------------- */
+
+/* Per(A_b) and its derivatives for a batch of matrices, in the same Gray-code
+ * pass as the Glynn sum (Supp. Eq. (S2) of arXiv 1606.05836, differentiated:
+ * dPer/da_ij = 2^-(n-1) sum_delta (prod delta) delta_j prod_{k != i} v_k; the
+ * paper itself has no gradient).  Plain FP64 (opts->prec must be PERM_FP64).
+ *
+ * dA:        batch matrices, matrix b at dA + b*strideA (complex elements), lda >= n.
+ * dPerm:     nullable [batch] Per(A_b).   dAbs2: nullable [batch] |Per(A_b)|^2.
+ * dMinor:    nullable [batch][n][n] dPer/da_ij = Per(A_b without row i, column j).
+ * dGradAbs2: nullable [batch][n][n] 2 Per conj(dPer/da_ij) = d|Per|^2/dRe a_ij
+ *            + i d|Per|^2/dIm a_ij (PyTorch's convention for a real loss).
+ * dWork:     256-byte-aligned, perm_grad_workspace_size() bytes: per lane an n x n
+ *            accumulator and snapshot (O(grid x 128 x 2 n^2 x 16) bytes, e.g.
+ *            0.64 GB at n = 32).  The batch runs item after item on `stream`.
+ * 1 <= n <= PERM_GRAD_MAX_N (n = 0 gives Per = 1, no derivatives). */
+#define PERM_GRAD_MAX_N 32
+size_t perm_grad_workspace_size(int n, const perm_opts* opts);
+int perm_grad(const perm_c128* dA, int n, int lda, int batch, int64_t strideA, perm_c128* dPerm, double* dAbs2,
+              perm_c128* dMinor, perm_c128* dGradAbs2, void* dWork, size_t workBytes, const perm_opts* opts,
+              void* stream);
+
 /* --- without caller memory ----------------------------------------------- */
 
 /* perm_glynn without a workspace argument: the same computation and kernel as

@@ -10,6 +10,11 @@ Functions mirror the C entry points:
 * :func:`glynn`  -- Per(A), BB/FG formula (Supp. Eq. (S2), Algorithm 2 of arXiv 1606.05836)
 * :func:`ryser`  -- Per(A), Ryser formula (Supp. Eq. (S1), Algorithm 1)
 * :func:`glynn_range`, :func:`ryser_range` -- partial sums over a Gray-index range
+* :func:`batched`, :class:`BatchedPermanents` -- many permanents of mixed sizes in
+  one persistent launch (CUDA-graph capture, autotuned launch shape)
+* :func:`prob` -- Eq. (1): |Per(U_ST)|^2 / (prod s_i! prod t_j!) for one (S, T)
+* :func:`grad`, :class:`PermAbs2` -- the adjoint: dPer/dA and d|Per|^2/dA in the
+  same Gray-code pass, behind a torch.autograd.Function
 """
 from __future__ import annotations
 
@@ -21,7 +26,7 @@ from . import _native
 from ._native import PERM_MAX_N, PRECISIONS, Opts, PermError
 
 __all__ = ["glynn", "ryser", "glynn_range", "ryser_range", "workspace_size", "PermError", "PERM_MAX_N",
-           "PRECISIONS", "library"]
+           "PRECISIONS", "library", "batched", "BatchedPermanents", "grad", "PermAbs2", "prob"]
 
 _workspaces: dict = {}
 
@@ -97,6 +102,37 @@ def ryser(A: torch.Tensor, prec="fp64", chunk_log2=0, block=0, grid=0) -> torch.
     return _run("perm_ryser", A, (), 1, prec=prec, chunk_log2=chunk_log2, block=block, grid=grid)[0]
 
 
+def prob(U: torch.Tensor, s, t, prec="fp64", chunk_log2=0, block=0, grid=0):
+    """Eq. (1) for input occupations s and output occupations t of the m x m unitary U
+    (complex128 CUDA tensor, U[i][j] = amplitude input i -> output j).  Returns
+    (probability, Per(U_ST)) as Python numbers; synchronises the current stream."""
+    import numpy as np
+
+    lib = library()
+    U, m, ldu = _matrix(U)
+    s = np.ascontiguousarray(np.asarray(s, dtype=np.int32))
+    t = np.ascontiguousarray(np.asarray(t, dtype=np.int32))
+    if s.shape != (m,) or t.shape != (m,):
+        raise ValueError("occupation vectors must have length m = %d" % m)
+    n = int(s.sum())
+    o = _opts(prec=prec, chunk_log2=chunk_log2, block=block, grid=grid)
+    dev = U.device
+    with torch.cuda.device(dev):
+        nbytes = int(lib.prob_sample_workspace_size(n, ctypes.byref(o)))
+        if nbytes == 0:
+            raise ValueError("photon number %d outside 0..%d" % (n, PERM_MAX_N))
+        ws = _workspace(dev, nbytes + 256)
+        base = (ws.data_ptr() + 255) & ~255
+        p = ctypes.c_double(0.0)
+        per = (ctypes.c_double * 2)()
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        st = lib.prob_sample(ctypes.c_void_p(U.data_ptr()), m, ldu, s.ctypes.data_as(i32p), t.ctypes.data_as(i32p),
+                             ctypes.byref(p), ctypes.cast(per, ctypes.c_void_p), ctypes.c_void_p(base),
+                             nbytes, ctypes.byref(o), ctypes.c_void_p(_stream_ptr(dev)))
+    _native.check(st, "prob_sample")
+    return p.value, complex(per[0], per[1])
+
+
 def _range(fname, A, k_begin, k_end, **opts):
     out = _run(fname, A, (ctypes.c_uint64(int(k_begin)), ctypes.c_uint64(int(k_end))), 2, **opts)
     return out  # (hi, lo)
@@ -110,3 +146,7 @@ def glynn_range(A, k_begin: int, k_end: int, prec="fp64", chunk_log2=0, block=0,
 def ryser_range(A, k_begin: int, k_end: int, prec="fp64", chunk_log2=0, block=0, grid=0) -> torch.Tensor:
     """Un-normalised Ryser partial sum over Gray indices [k_begin, k_end): tensor (hi, lo)."""
     return _range("perm_ryser_range", A, k_begin, k_end, prec=prec, chunk_log2=chunk_log2, block=block, grid=grid)
+
+
+from .batch import BatchedPermanents, batched  # noqa: E402
+from .grad import PermAbs2, grad  # noqa: E402

@@ -24,6 +24,10 @@ EXPORTS = (
     "perm_ryser_range",
     "perm_batched_workspace_size",
     "perm_batched",
+    "prob_sample_workspace_size",
+    "prob_sample",
+    "perm_grad_workspace_size",
+    "perm_grad",
     "perm_glynn_noalloc",
     "perm_strerror",
     "perm_last_cuda_error",
@@ -73,6 +77,14 @@ def load(path: str | None = None):
     lib.perm_batched_workspace_size.restype = sz
     lib.perm_batched.argtypes = [vp, vp, vp, i32p, i32, i32, vp, vp, vp, vp, sz, op, vp]
     lib.perm_batched.restype = i32
+    lib.prob_sample_workspace_size.argtypes = [i32, op]
+    lib.prob_sample_workspace_size.restype = sz
+    lib.prob_sample.argtypes = [vp, i32, i32, i32p, i32p, ctypes.POINTER(ctypes.c_double), vp, vp, sz, op, vp]
+    lib.prob_sample.restype = i32
+    lib.perm_grad_workspace_size.argtypes = [i32, op]
+    lib.perm_grad_workspace_size.restype = sz
+    lib.perm_grad.argtypes = [vp, i32, i32, i32, ctypes.c_int64, vp, vp, vp, vp, vp, sz, op, vp]
+    lib.perm_grad.restype = i32
     lib.perm_glynn_noalloc.argtypes = [vp, i32, i32, vp, op, vp]
     lib.perm_glynn_noalloc.restype = i32
     lib.perm_strerror.argtypes = [i32]

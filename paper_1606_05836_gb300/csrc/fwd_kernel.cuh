@@ -49,12 +49,13 @@ struct Stride {
 // (no rounding), and it keeps FP32 products of the R2 rung inside FP32's
 // exponent range.  Returns sum_i s_i (identical in every block).
 template <int N>
-__device__ int stage_matrix(const FwdArgs& a, double2* Acol, double2* Step, int* s_row) {
+__device__ int stage_matrix(const double2* __restrict__ A, int lda, int kind, double2* Acol, double2* Step,
+                            int* s_row) {
   const int n = N;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double nrm = 0.0;
     for (int j = 0; j < n; j++) {
-      const double2 v = a.A[(size_t)i * a.lda + j];
+      const double2 v = A[(size_t)i * lda + j];
       nrm = fma(v.x, v.x, nrm);
       nrm = fma(v.y, v.y, nrm);
     }
@@ -67,11 +68,11 @@ __device__ int stage_matrix(const FwdArgs& a, double2* Acol, double2* Step, int*
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     const int i = idx / n, j = idx % n;
     const double f = pow2_double(s_row[i]);
-    const double2 v = a.A[(size_t)i * a.lda + j];
+    const double2 v = A[(size_t)i * lda + j];
     Acol[j * Stride<N>::value + i] = make_double2(v.x * f, v.y * f);
   }
   __syncthreads();
-  if (a.kind == KIND_GLYNN) {
+  if (kind == KIND_GLYNN) {
     for (int idx = threadIdx.x; idx < (n - 1) * n; idx += blockDim.x) {
       const int b = idx / n, i = idx % n;
       const double2 v = Acol[(b + 1) * Stride<N>::value + i];
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(256, 1) fwd_kernel(FwdArgs a) {
   double2* Step = (a.kind == KIND_GLYNN) ? smem + N * NP : smem;
   __shared__ int s_row[N];
 
-  const int scale_exp = stage_matrix<N>(a, Acol, Step, s_row);
+  const int scale_exp = stage_matrix<N>(a.A, a.lda, a.kind, Acol, Step, s_row);
   const double nz = a.neg_zero;
 
   const uint64_t T = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -1,0 +1,233 @@
+// Adjoint of the Glynn permanent in the same Gray-code pass (Supp. Eq. (S2)).
+//
+// dPer/da_ij = 2^-(n-1) sum_delta (prod delta) delta_j prod_{k != i} v_k(delta),
+// v_i = sum_j delta_j a_ij.  Per term, q_i = prod_{k != i} v_k comes from one
+// suffix pass (stored per lane in shared memory) and one prefix pass — 3(n-2)
+// complex multiplies, no division (a row sum may be exactly zero).  With
+// w_i = (prod delta) q_i, G_ij = sum over terms of w_i delta_j is accumulated at
+// O(n) per term: S_i = running sum of w_i (shared memory), and only when the Gray
+// code flips column j is G_:j += delta_j^old (S - snap_:j), snap_:j = S
+// (delta_j is constant between its flips).  The per-lane G and snap (n x n each)
+// live in the caller's workspace, lane-interleaved so every warp access is
+// coalesced; a second kernel sums the lanes in a fixed order.
+#pragma once
+#include "fwd_kernel.cuh"
+
+namespace permk {
+
+constexpr int GRAD_MAX_N = 32;
+constexpr int GRAD_BLOCK = 128;
+
+struct GradArgs {
+  const double2* A;
+  int lda;
+  int chunk_log2;
+  uint64_t per_q, per_r;  // floor/ceil split of the 2^(n-1) Gray indices over the lanes
+  double neg_zero;
+  double2* state;         // [(i*N + j)*2 + {0: G, 1: snap}][P]
+  long long P;            // lanes in the grid (= state stride)
+  double* partials;       // forward Per: 4 doubles per block
+  int* scale_exp;         // [1 + N]: sum_i s_i, then s_i (written by block 0)
+};
+
+template <int N>
+__device__ __forceinline__ double2* gstate(const GradArgs& a, int i, int j, int w, long long T) {
+  return a.state + ((long long)((i * N + j) * 2 + w)) * a.P + T;
+}
+
+// G_:j += delta (S - snap_:j); snap_:j = S   (delta = +-1 as a sign mask)
+template <int N>
+__device__ __forceinline__ void flush_column(const GradArgs& a, int j, unsigned long long neg_mask,
+                                             const double2* S, int B, long long T) {
+  const double sgn = xor_sign(1.0, neg_mask);
+#pragma unroll 8
+  for (int i = 0; i < N; i++) {
+    const double2 s = S[i * B];
+    double2* gp = gstate<N>(a, i, j, 0, T);
+    double2* sp = gstate<N>(a, i, j, 1, T);
+    const double2 snap = *sp;
+    double2 g = *gp;
+    g.x = fma(sgn, s.x - snap.x, g.x);
+    g.y = fma(sgn, s.y - snap.y, g.y);
+    *gp = g;
+    *sp = s;
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(GRAD_BLOCK, 1) grad_kernel(GradArgs a) {
+  extern __shared__ double2 smem[];
+  constexpr int NP = Stride<N>::value;
+  double2* Acol = smem;
+  double2* Step = smem + N * NP;
+  const int B = blockDim.x;
+  double2* suf = smem + 2 * N * NP + threadIdx.x;        // suf[i * B]
+  double2* S = smem + 2 * N * NP + N * B + threadIdx.x;  // S[i * B]
+  __shared__ int s_row[N];
+  __shared__ dd wsum[2][GRAD_BLOCK / 32];
+
+  const int scale_exp = stage_matrix<N>(a.A, a.lda, KIND_GLYNN, Acol, Step, s_row);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.scale_exp[0] = scale_exp;
+    for (int i = 0; i < N; i++) a.scale_exp[1 + i] = s_row[i];
+  }
+  const double nz = a.neg_zero;
+  const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t kb = a.per_q * (uint64_t)T + ((uint64_t)T < a.per_r ? (uint64_t)T : a.per_r);
+  const uint64_t ke = kb + a.per_q + ((uint64_t)T < a.per_r ? 1 : 0);
+  const uint64_t CH = 1ull << a.chunk_log2;
+
+  // per-lane state starts at zero
+  for (int i = 0; i < N; i++) {
+    S[i * B] = make_double2(0.0, 0.0);
+    for (int j = 0; j < N; j++) {
+      *gstate<N>(a, i, j, 0, T) = make_double2(0.0, 0.0);
+      *gstate<N>(a, i, j, 1, T) = make_double2(0.0, 0.0);
+    }
+  }
+
+  double ar = 0.0, ai = 0.0;
+  uint64_t k = kb;
+  uint64_t g = kb ^ (kb >> 1);
+  while (k < ke) {
+    const uint64_t c1 = (ke - k > CH) ? k + CH : ke;
+    double vr[N], vi[N];
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      vr[i] = 0.0;
+      vi[i] = 0.0;
+    }
+#pragma unroll 1
+    for (int j = 0; j < N; j++) {
+      const double coef = (j == 0) ? 1.0 : (((g >> (j - 1)) & 1ull) ? -1.0 : 1.0);
+      const double2* col = Acol + j * NP;
+#pragma unroll
+      for (int i = 0; i < N; i++) {
+        const double2 x = col[i];
+        vr[i] = fma(coef, x.x, vr[i]);
+        vi[i] = fma(coef, x.y, vi[i]);
+      }
+    }
+#pragma unroll 1
+    while (true) {
+      const unsigned long long smask = (k & 1ull) << 63;  // (prod delta) = (-1)^(k & 1)
+      const double sgn = xor_sign(1.0, smask);
+      if (N == 1) {
+        // q_0 = 1 (empty product); Per term = v_0
+        double2 s0 = S[0];
+        s0.x += sgn;
+        S[0] = s0;
+        ar = fma(sgn, vr[0], ar);
+        ai = fma(sgn, vi[0], ai);
+      } else {
+        // suffix products suf_i = v_i ... v_{N-1}, i >= 1
+        double pr = vr[N - 1], pi = vi[N - 1];
+        suf[(N - 1) * B] = make_double2(pr, pi);
+#pragma unroll
+        for (int i = N - 2; i >= 1; i--) {
+          cmul_inplace<3>(pr, pi, vr[i], vi[i], nz);
+          suf[i * B] = make_double2(pr, pi);
+        }
+        // prefix pass: q_i = (v_0 ... v_{i-1}) suf_{i+1}
+        double qr = pr, qi = pi;  // q_0 = suf_1
+        double2 s0 = S[0];
+        s0.x = fma(sgn, qr, s0.x);
+        s0.y = fma(sgn, qi, s0.y);
+        S[0] = s0;
+        double er = vr[0], ei = vi[0];  // prefix v_0 ... v_{i-1}
+#pragma unroll
+        for (int i = 1; i < N - 1; i++) {
+          const double2 sf = suf[(i + 1) * B];
+          qr = er;
+          qi = ei;
+          cmul_inplace<3>(qr, qi, sf.x, sf.y, nz);
+          double2 si = S[i * B];
+          si.x = fma(sgn, qr, si.x);
+          si.y = fma(sgn, qi, si.y);
+          S[i * B] = si;
+          cmul_inplace<3>(er, ei, vr[i], vi[i], nz);
+        }
+        // q_{N-1} = prefix of all but the last row
+        double2 sl = S[(N - 1) * B];
+        sl.x = fma(sgn, er, sl.x);
+        sl.y = fma(sgn, ei, sl.y);
+        S[(N - 1) * B] = sl;
+        // forward term: (prod delta) * prefix * v_{N-1}
+        er = xor_sign(er, smask);
+        ei = xor_sign(ei, smask);
+        ar = fma(er, vr[N - 1], ar);
+        ar = fma(-ei, vi[N - 1], ar);
+        ai = fma(er, vi[N - 1], ai);
+        ai = fma(ei, vr[N - 1], ai);
+      }
+      ++k;
+      if (k >= ke) break;
+      // column j = b+1 flips: flush its segment with its old sign, then step
+      const int b = __ffsll((long long)k) - 1;
+      const unsigned long long old_neg = ((g >> b) & 1ull) << 63;
+      flush_column<N>(a, b + 1, old_neg, S, B, T);
+      g ^= 1ull << b;
+      if (k >= c1) break;  // next chunk: recompute the row sums from g
+      // bit now set: delta_{b+2} became -1, subtract 2a; bit now clear: add
+      const double su = xor_sign(1.0, ((g >> b) & 1ull) << 63);
+      const double2* col = Step + b * NP;
+#pragma unroll
+      for (int i = 0; i < N; i++) {
+        const double2 x = col[i];
+        vr[i] = fma(su, x.x, vr[i]);
+        vi[i] = fma(su, x.y, vi[i]);
+      }
+    }
+  }
+  // final flush of every column with its current sign (column 0 is always +1)
+  for (int j = 0; j < N; j++) {
+    const unsigned long long neg = (j == 0) ? 0ull : (((g >> (j - 1)) & 1ull) << 63);
+    flush_column<N>(a, j, neg, S, B, T);
+  }
+
+  // forward permanent: block partials (the reduce kernel sums them in order)
+  dd sr{ar, 0.0}, si{ai, 0.0};
+  warp_sum_dd(sr, si);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    wsum[0][warp] = sr;
+    wsum[1][warp] = si;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    dd br = wsum[0][0], bi = wsum[1][0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+      br = dd_add(br, wsum[0][w]);
+      bi = dd_add(bi, wsum[1][w]);
+    }
+    double* p = a.partials + 4 * (size_t)blockIdx.x;
+    p[0] = br.hi;
+    p[1] = br.lo;
+    p[2] = bi.hi;
+    p[3] = bi.lo;
+  }
+}
+
+struct GradReduceArgs {
+  const double2* state;
+  long long P;
+  int n;
+  const double* partials;
+  int nblocks;
+  const int* scale_exp;  // [1 + n]
+  double2* perm;         // nullable: Per
+  double2* minor;        // nullable: dPer/da_ij, row-major n x n
+  double2* grad_abs2;    // nullable: 2 Per conj(dPer/da_ij)
+  double* abs2;          // nullable: |Per|^2
+};
+
+template <int N>
+int launch_grad(const GradArgs& a, int grid, cudaStream_t s);
+template <int N>
+int grad_blocks_per_sm(int* out);
+
+inline size_t grad_smem_bytes(int N) {
+  return (size_t)2 * N * (N | 1) * sizeof(double2) + (size_t)2 * N * GRAD_BLOCK * sizeof(double2);
+}
+
+}  // namespace permk

@@ -176,6 +176,35 @@ int run_fwd(const perm_c128* dA, int n, int lda, int kind, uint64_t k_begin, uin
   return PERM_OK;
 }
 
+// --- prob_sample helpers -----------------------------------------------------
+
+struct GatherArgs {
+  const double2* U;
+  int ldu;
+  int n;
+  int rows[PERM_MAX_N];
+  int cols[PERM_MAX_N];
+  double2* out;  // n x n, row-major
+};
+
+// U_ST[r][c] = U[rows[r]][cols[c]]
+__global__ void gather_ust_kernel(GatherArgs g) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.n * g.n; idx += gridDim.x * blockDim.x) {
+    const int r = idx / g.n, c = idx % g.n;
+    g.out[idx] = g.U[(size_t)g.rows[r] * g.ldu + g.cols[c]];
+  }
+}
+
+// Eq. (1): Pr = |Per|^2 * scale, scale = 1 / (prod s_i! prod t_j!)
+__global__ void prob_epilogue_kernel(const double2* per, double scale, double* prob) {
+  const double2 p = per[0];
+  prob[0] = fma(p.x, p.x, p.y * p.y) * scale;
+}
+
+size_t prob_ws_offset_ust() { return 0; }
+size_t prob_ws_offset_res(int n) { return ((size_t)n * n * sizeof(double2) + 255) & ~(size_t)255; }
+size_t prob_ws_offset_fwd(int n) { return prob_ws_offset_res(n) + 256; }
+
 }  // namespace
 
 void permk::record_cuda_error(int err) { g_last_cuda = err; }
@@ -215,6 +244,67 @@ int perm_ryser_range(const perm_c128* dA, int n, int lda, uint64_t k_begin, uint
                      void* dWork, size_t workBytes, const perm_opts* opts, void* stream) {
   if (n < 1) return PERM_ERANGE;
   return run_fwd(dA, n, lda, permk::KIND_RYSER, k_begin, k_end, 1, dOut, dWork, workBytes, opts, stream);
+}
+
+
+size_t prob_sample_workspace_size(int n, const perm_opts* opts) {
+  if (n < 0 || n > PERM_MAX_N) return 0;
+  const size_t fwd = n >= 1 ? perm_workspace_size(n, opts) : 256;
+  if (fwd == 0) return 0;
+  return prob_ws_offset_fwd(n) + fwd;
+}
+
+int prob_sample(const perm_c128* dU, int m, int ldu, const int32_t* hS, const int32_t* hT, double* hProb,
+                perm_c128* hPerm, void* dWork, size_t workBytes, const perm_opts* opts, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (m < 1 || !dU || ldu < m || !hS || !hT || !hProb || !dWork) return PERM_EINVAL;
+  if (((uintptr_t)dU & 15u) || ((uintptr_t)dWork & 255u)) return PERM_EINVAL;
+  GatherArgs g;
+  int n = 0, nt = 0;
+  double denom = 1.0;
+  for (int i = 0; i < m; i++) {
+    if (hS[i] < 0 || hT[i] < 0) return PERM_EINVAL;
+    for (int k = 2; k <= hS[i]; k++) denom *= (double)k;
+    for (int k = 2; k <= hT[i]; k++) denom *= (double)k;
+    for (int k = 0; k < hS[i]; k++) {
+      if (n >= PERM_MAX_N) return PERM_ERANGE;
+      g.rows[n++] = i;
+    }
+    for (int k = 0; k < hT[i]; k++) {
+      if (nt >= PERM_MAX_N) return PERM_ERANGE;
+      g.cols[nt++] = i;
+    }
+  }
+  if (n != nt) return PERM_EINVAL;
+  if (workBytes < prob_sample_workspace_size(n, opts)) return PERM_ENOMEM;
+  char* w = (char*)dWork;
+  double2* ust = (double2*)(w + prob_ws_offset_ust());
+  double2* res = (double2*)(w + prob_ws_offset_res(n));
+  double* prob = (double*)(w + prob_ws_offset_res(n) + 64);
+  g.U = (const double2*)dU;
+  g.ldu = ldu;
+  g.n = n;
+  g.out = ust;
+  if (n > 0) {
+    gather_ust_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(g);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail_cuda(e);
+  }
+  int st = run_fwd((const perm_c128*)ust, n, n, permk::KIND_GLYNN, 0, n >= 1 ? (1ull << (n - 1)) : 0, 0,
+                   (perm_c128*)res, w + prob_ws_offset_fwd(n), workBytes - prob_ws_offset_fwd(n), opts, stream);
+  if (st) return st;
+  prob_epilogue_kernel<<<1, 1, 0, s>>>(res, 1.0 / denom, prob);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_cuda(e);
+  e = cudaMemcpyAsync(hProb, prob, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return fail_cuda(e);
+  if (hPerm) {
+    e = cudaMemcpyAsync(hPerm, res, sizeof(perm_c128), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return fail_cuda(e);
+  }
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail_cuda(e);
+  return PERM_OK;
 }
 
 const char* perm_strerror(int status) {

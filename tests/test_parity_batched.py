@@ -1,0 +1,112 @@
+"""GPU parity of the batched form (perm_batched: one persistent size-bucketed
+launch, per-item reduce and the Eq. (1) probability epilogue) against the oracle,
+through the C ABI, plus its CUDA-graph replay and its device-side guards."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+from gpu_util import REL_TOL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pg():
+    import paper_1606_05836_gb300 as pg
+    from paper_1606_05836_gb300 import build
+    build.build()
+    pg.library()
+    return pg
+
+
+def _mixed(count, n_lo, n_hi, seed):
+    g = np.random.default_rng(seed)
+    return [S.gaussian(int(n), seed * 1000 + i, 1.0) for i, n in enumerate(g.integers(n_lo, n_hi + 1, size=count))]
+
+
+@pytest.mark.parametrize("method", ["glynn", "ryser"])
+def test_batched_small_mixed_all_rungs(pg, method):
+    mats = _mixed(48, 1, 14, 1)
+    want = [oracle.perm_def(A) if A.shape[0] <= 8 else oracle.ryser(A) for A in mats]
+    tol = {"fp64": REL_TOL, "fp64_dd": REL_TOL, "fp32p_dd": 1e-4 if method == "glynn" else 1e-2}
+    for prec in ("fp64", "fp64_dd", "fp32p_dd"):
+        per, _ = pg.batched(mats, method=method, prec=prec)
+        got = per.cpu().numpy()
+        for i, w in enumerate(want):
+            assert w.rel_err(got[i]) < tol[prec], (prec, i, mats[i].shape[0], got[i], w.hi)
+
+
+def test_batched_matches_single_permanent_path(pg):
+    mats = _mixed(40, 14, 22, 2)
+    import torch
+    per, _ = pg.batched(mats, method="glynn", unit_log2=5)  # many units per item
+    got = per.cpu().numpy()
+    for i, A in enumerate(mats):
+        single = complex(pg.glynn(torch.as_tensor(A).cuda()).cpu().item())
+        assert abs(got[i] - single) <= REL_TOL * abs(single)
+
+
+def test_batched_probabilities_with_collisions(pg):
+    """Eq. (1): output patterns of one Haar unitary, one photon per input mode,
+    20 % of the outputs with repeated columns; prob = |Per(U_ST)|^2 / prod t_j!."""
+    U = S.haar_unitary(30, 7)
+    mats, ns, rows, cols, collide = S.batch_patterns(U, 60, 2, 9, 8)
+    assert collide.any() and not collide.all()
+    scale, s_vecs, t_vecs = [], [], []
+    for r, c in zip(rows, cols):
+        s = np.zeros(30, dtype=np.int32)
+        t = np.zeros(30, dtype=np.int32)
+        s[r] = 1
+        for j in c:
+            t[j] += 1
+        s_vecs.append(s)
+        t_vecs.append(t)
+        scale.append(1.0 / float(np.prod([math.factorial(int(x)) for x in t])))
+    per, prob = pg.batched(mats, method="glynn", scale=scale)
+    per, prob = per.cpu().numpy(), prob.cpu().numpy()
+    for i in range(len(mats)):
+        p_want, per_want = oracle.prob(U, s_vecs[i], t_vecs[i])
+        assert per_want.rel_err(per[i]) < REL_TOL
+        assert abs(prob[i] - p_want) <= 1e-9 * p_want + 1e-300
+
+
+def test_batched_graph_replay_and_autotune(pg, tmp_path, monkeypatch):
+    from paper_1606_05836_gb300 import batch as B
+    monkeypatch.setattr(B, "TUNE_CACHE", str(tmp_path / "tune.json"))
+    mats = _mixed(64, 8, 18, 3)
+    bp = B.BatchedPermanents(mats, method="glynn")
+    eager = bp.run()[0].clone()
+    best = bp.autotune(candidates=[(7, 64), (9, 128)], reps=1)
+    assert best["unit_log2"] in (7, 9)
+    bp.capture()
+    for _ in range(2):
+        per, _ = bp.replay()
+        assert np.allclose(per.cpu().numpy(), eager.cpu().numpy(), rtol=1e-12, atol=0)
+    again = B.BatchedPermanents(mats, method="glynn")
+    assert again.autotune(candidates=[(7, 64)], reps=1) == best  # served from the cache
+
+
+def test_batched_device_guards_give_nan_not_a_fault(pg):
+    """Sizes on the device that disagree with the host sizes: the planner
+    refuses the batch and the outputs are NaN (no out-of-bounds access)."""
+    import ctypes
+    import torch
+    from paper_1606_05836_gb300 import batch as B
+    mats = [S.gaussian(5, 11, 1.0), S.gaussian(5, 12, 1.0)]
+    bp = B.BatchedPermanents(mats)
+    bp.ns.copy_(torch.tensor([5, 33], dtype=torch.int32))   # n beyond the batched maximum
+    per, prob = bp.run()
+    assert torch.isnan(per.real).all() and torch.isnan(prob).all()
+    bp = B.BatchedPermanents(mats)
+    bp.ns.copy_(torch.tensor([5, 20], dtype=torch.int32))   # more work than the workspace was sized for
+    bp.packed = torch.zeros(500, dtype=torch.complex128, device="cuda")
+    per, _ = bp.run()
+    assert torch.isnan(per.real).all()
+
+
+def test_batched_empty(pg):
+    per, prob = pg.batched([])
+    assert per.numel() == 0
