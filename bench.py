@@ -53,6 +53,12 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched / compensated / adjoint forms")
+    ap.add_argument("--form", choices=["sweep", "batched", "adjoint"], default="sweep",
+                    help="sweep = the metric above (default); batched / adjoint time only that form "
+                         "(for profiling) and print its own JSON line")
+    ap.add_argument("--adjoint-n", type=int, default=24)
+    ap.add_argument("--adjoint-batch", type=int, default=64)
     return ap.parse_args()
 
 
@@ -149,6 +155,35 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# DRAM traffic of the dominant kernel, from a committed ncu summary
+# ---------------------------------------------------------------------------
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fwd_kernel_traffic.json")
+KERNEL_SOURCES = ("common.cuh", "fwd_kernel.cuh", "fwd_inst.cu")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1606_05836_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(n: int):
+    """dram read+write bytes per launch of fwd_kernel<n> from the ncu capture,
+    or None when there is none or the kernel sources changed since it was taken."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_sha256") != kernel_source_hash() or int(rec.get("n", -1)) != n:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
 # the oracle on the host cores
 # ---------------------------------------------------------------------------
 def oracle_rate(items, seconds: float, threads: int):
@@ -224,6 +259,79 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ---------------------------------------------------------------------------
+# the other forms, each against the plain form on the same GPU
+# ---------------------------------------------------------------------------
+def measure_forms(dev, plain_rate):
+    """Batched (graph replay), compensated rungs R1/R2 and the adjoint, with errors."""
+    import math
+
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1606_05836_gb300 as pg
+    import synthetic as S
+    from paper_1606_05836_gb300 import batch as B
+
+    def timed(fn, reps=1):
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize(dev)
+            t = e0.elapsed_time(e1) / 1e3
+            best = t if best is None else min(best, t)
+        return best
+
+    forms = {}
+    # precision ladder: rates at n = 32 (Gaussian var 1/n^2), errors at n = 20 vs the quad oracle
+    A32 = torch.as_tensor(S.gaussian(32, 0)).to(dev)
+    A20h = S.gaussian(20, 0)
+    A20 = torch.as_tensor(A20h).to(dev)
+    want20 = oracle.glynn(A20h)
+    for prec in ("fp64", "fp64_dd", "fp32p_dd"):
+        pg.glynn(A32, prec=prec)
+        t = timed(lambda: pg.glynn(A32, prec=prec))
+        err = want20.rel_err(complex(pg.glynn(A20, prec=prec).cpu().item()))
+        forms["glynn_n32_" + prec] = {"terms_per_s": 2 ** 31 / t, "vs_plain_glynn": None, "rel_err_n20_vs_oracle": err}
+    base = forms["glynn_n32_fp64"]["terms_per_s"]
+    for k in list(forms):
+        forms[k]["vs_plain_glynn"] = forms[k]["terms_per_s"] / base
+    # batched: 4096 output patterns of one Haar 1000 x 1000 unitary, n in 8..24, 20 % collisions
+    U = S.haar_unitary(1000, 0)
+    mats, ns, rows, cols, collide = S.batch_patterns(U, 4096, 8, 24, 1)
+    scale = [1.0 / float(np.prod([math.factorial(int(x)) for x in np.bincount(c)])) for c in cols]
+    bp = B.BatchedPermanents(mats, method="glynn", scale=scale)
+    tuned = bp.autotune(candidates=[(9, 128), (11, 64), (11, 128), (13, 128)], reps=1)
+    bp.capture()
+    bp.replay()
+    t = timed(bp.replay, reps=3)
+    terms = int(sum(2 ** (int(n) - 1) for n in ns))
+    per = bp.out.cpu().numpy()
+    # sampled parity of the batch against the oracle (items with n <= 16)
+    small = [i for i in range(len(mats)) if ns[i] <= 14][:8]
+    berr = max(oracle.glynn(mats[i]).rel_err(per[i]) for i in small) if small else None
+    forms["batched_4096_n8-24"] = {"terms_per_s": terms / t, "perms_per_s": len(mats) / t, "s_per_replay": t,
+                                   "vs_plain_glynn": terms / t / base, "collision_items": int(collide.sum()),
+                                   "tuned": {"unit_log2": tuned["unit_log2"], "block": tuned["block"]},
+                                   "max_rel_err_sampled_vs_oracle": berr}
+    # adjoint: batch of 64 Gaussian matrices at n = 24
+    G = torch.as_tensor(np.stack([S.gaussian(24, b) for b in range(64)])).to(dev)
+    pg.grad(G[:1])
+    tg = timed(lambda: pg.grad(G))
+    tf = timed(lambda: [pg.glynn(G[b]) for b in range(64)])
+    _, _, M, _ = pg.grad(G[:1])
+    A0 = G[0].cpu().numpy()
+    P0 = complex(pg.glynn(G[0]).cpu().item())
+    lap = float(np.max(np.abs(np.sum(A0 * M[0].cpu().numpy(), axis=1) - P0)) / abs(P0))
+    forms["adjoint_64_n24"] = {"terms_per_s": 64 * 2 ** 23 / tg, "s": tg, "cost_vs_plain_same_batch": tg / tf,
+                               "laplace_identity_rel_err": lap}
+    return forms
 
 
 # ---------------------------------------------------------------------------
@@ -352,6 +460,7 @@ def run_ours(args):
     # GB300: 2 FP64 FMA lanes per clock per SM (0.5 per sub-partition) = 4 flop/clk/SM
     peak_fp64 = sms * 4 * sm_max_mhz * 1e6
     achieved = sum(f for f, _ in dom) / (sum(ms for _, ms in dom) / 1e3) if dom else None
+    traffic = measured_traffic(nmax)
     roofline = {
         "bound": "alu", "pipe": "fp64",
         "kernel": "fwd_kernel<N=%d> (Glynn+Ryser, %s)" % (nmax, args.prec),
@@ -359,7 +468,7 @@ def run_ours(args):
         "frac": (achieved / peak_fp64) if achieved else None,
         "peak_source": "derived: %d SMs x 4 FP64 flop/clk/SM x %.0f MHz" % (sms, sm_max_mhz),
         "flops_per_term": "8n-4 (2n update + 6(n-1) product + 2 accumulate)",
-        "traffic": None,
+        "traffic": traffic,
     }
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -369,14 +478,65 @@ def run_ours(args):
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": "quad-precision oracle, first %d Gray-order terms of each (method, n) item of step 0, "
                          "%.1f s" % (sample, dt)}
+    forms = None
+    if world == 1 and not args.no_forms:
+        forms = measure_forms(dev, value)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec != "fp32p_dd" else "f64+f32",
         "data": "synthetic", "config": config_dict(args, ns, kinds, world), "roofline": roofline,
-        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "forms": forms,
     }
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_single_form(args):
+    """Time one form on its own (used for profiling runs); prints its JSON line."""
+    import numpy as np
+    import torch
+
+    import paper_1606_05836_gb300 as pg
+    import synthetic as S
+
+    dev = torch.device("cuda", 0)
+    if args.form == "adjoint":
+        n, b = args.adjoint_n, args.adjoint_batch
+        G = torch.as_tensor(np.stack([S.gaussian(n, i) for i in range(b)])).to(dev)
+        for _ in range(args.warmup):
+            pg.grad(G[:1])
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            pg.grad(G)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        t = e0.elapsed_time(e1) / 1e3
+        print(json.dumps({"form": "adjoint", "n": n, "batch": b, "steps": args.steps,
+                          "terms_per_s": args.steps * b * 2 ** (n - 1) / t}), flush=True)
+    else:
+        import math
+
+        from paper_1606_05836_gb300 import batch as B
+        U = S.haar_unitary(1000, 0)
+        mats, ns, rows, cols, collide = S.batch_patterns(U, 4096, 8, 24, 1)
+        scale = [1.0 / float(np.prod([math.factorial(int(x)) for x in np.bincount(c)])) for c in cols]
+        bp = B.BatchedPermanents(mats, method="glynn", scale=scale)
+        for _ in range(args.warmup):
+            bp.run()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            bp.run()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        t = e0.elapsed_time(e1) / 1e3
+        terms = int(sum(2 ** (int(n) - 1) for n in ns))
+        print(json.dumps({"form": "batched", "count": len(mats), "steps": args.steps,
+                          "terms_per_s": args.steps * terms / t}), flush=True)
     return 0
 
 
@@ -384,6 +544,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.form != "sweep":
+        return run_single_form(args)
     return run_ours(args)
 
 

@@ -13,6 +13,8 @@ evaluates, and which passage of arXiv 1606.05836 it follows:
 * :func:`ryser`         -- Ryser's formula, Supp. Eq. (S1), subsets from the bits
                            of the iteration index as in Algorithm 1 (n <= 30).
 * :func:`glynn`         -- the BB/FG formula, Supp. Eq. (S2), Algorithm 2 (n <= 30).
+* :func:`glynn_gray`    -- Eq. (S2) in reflected-Gray order with one-sign row-sum
+                           updates (the O(n 2^n) order the paper names), n <= 40.
 * :func:`ryser_range`,
   :func:`glynn_range`   -- partial sums of the un-normalised terms over an index
                            range, binary or reflected-Gray index-to-set mapping.
@@ -57,6 +59,7 @@ def _load():
         lib.oracle_perm_def.argtypes = [ctypes.c_int, dp, dp]
         lib.oracle_ryser.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp]
         lib.oracle_glynn.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp]
+        lib.oracle_glynn_gray.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp]
         lib.oracle_ryser_range.argtypes = [ctypes.c_int, dp, u64, u64, ctypes.c_int, ctypes.c_int, dp]
         lib.oracle_glynn_range.argtypes = [ctypes.c_int, dp, u64, u64, ctypes.c_int, ctypes.c_int, dp]
         lib.oracle_ryser_z128.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
@@ -64,7 +67,7 @@ def _load():
         lib.oracle_minors.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp]
         lib.oracle_prob.argtypes = [ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int32),
                                     ctypes.POINTER(ctypes.c_int32), ctypes.c_int, dp, dp]
-        for f in ("oracle_perm_def", "oracle_ryser", "oracle_glynn", "oracle_ryser_range",
+        for f in ("oracle_perm_def", "oracle_ryser", "oracle_glynn", "oracle_glynn_gray", "oracle_ryser_range",
                   "oracle_glynn_range", "oracle_ryser_z128", "oracle_minors", "oracle_prob"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
@@ -135,6 +138,14 @@ def glynn(A, threads: int = 0) -> QC:
     A = _as_c128(A)
     out = np.zeros(4)
     _check(_load().oracle_glynn(A.shape[0], _dp(A), threads, _dp(out)), "glynn")
+    return _qc(out)
+
+
+def glynn_gray(A, threads: int = 0) -> QC:
+    """Per(A) by Eq. (S2) in reflected-Gray order (one sign flips per step), quad, n <= 40."""
+    A = _as_c128(A)
+    out = np.zeros(4)
+    _check(_load().oracle_glynn_gray(A.shape[0], _dp(A), threads, _dp(out)), "glynn_gray")
     return _qc(out)
 
 

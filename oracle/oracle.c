@@ -19,6 +19,12 @@
  *   oracle_glynn_range   partial sums of the BB/FG (Glynn) formula, Supp. Eq. (S2),
  *                        delta_1 = +1 and delta_{b+2} = -1 iff bit b of the index
  *                        (or of its Gray code) is set; complex _Float128.
+ *   oracle_glynn_gray    Eq. (S2) summed in reflected-Gray-code order, the
+ *                        execution order the paper names as the O(n 2^n)
+ *                        alternative (Supp. "Parallelization and Optimization"):
+ *                        consecutive delta vectors differ in one sign, so each
+ *                        row sum changes by +-2 a_ij; complex _Float128 with the
+ *                        row sums recomputed from scratch at every thread's start.
  *   oracle_ryser_z128    Eq. (S1) for integer matrices in unsigned __int128
  *                        arithmetic (exact modulo 2^128, hence exact whenever
  *                        |Per(A)| < 2^127).
@@ -240,6 +246,77 @@ int oracle_glynn(int n, const double* A, int nthreads, double* out4) {
   for (int i = 0; i < n - 1; i++) scale = scale / (q_t)2;
   qc_t s = {((q_t)r4[0] + (q_t)r4[1]) * scale, ((q_t)r4[2] + (q_t)r4[3]) * scale};
   store_result(s, out4);
+  return 0;
+}
+
+/* Per(A) by Eq. (S2) with the 2^{n-1} delta vectors taken in reflected-Gray order
+ * k = 0, 1, ..., delta_{b+2} = -1 iff bit b of k ^ (k >> 1) is set.  Each thread
+ * takes a contiguous range of k, computes the row sums of its first delta from
+ * scratch, then moves to the next delta by flipping the one sign that changes
+ * (row sums change by -+2 a_{i,b+1}).  Complex _Float128.  n <= 40. */
+int oracle_glynn_gray(int n, const double* A, int nthreads, double* out4) {
+  if (n < 0 || n > 40 || (n > 0 && !A) || !out4) return -1;
+  if (n == 0) { store_result(qc_one(), out4); return 0; }
+  const uint64_t total = 1ull << (n - 1);
+  int P = max_threads(nthreads);
+  qc_t* part = (qc_t*)calloc((size_t)P, sizeof(qc_t));
+  if (!part) return -1;
+  int fail = 0;
+#pragma omp parallel num_threads(P)
+  {
+#ifdef _OPENMP
+    int rank = omp_get_thread_num();
+    int np = omp_get_num_threads();
+#else
+    int rank = 0, np = 1;
+#endif
+    uint64_t len = (total + (uint64_t)np - 1) / (uint64_t)np;
+    uint64_t start = (uint64_t)rank * len;
+    uint64_t end = start + len;
+    if (start > total) start = total;
+    if (end > total) end = total;
+    qc_t* v = (qc_t*)malloc(sizeof(qc_t) * (size_t)n);
+    qc_t acc = qc_zero();
+    if (!v) {
+#pragma omp atomic write
+      fail = 1;
+    } else if (start < end) {
+      uint64_t code = start ^ (start >> 1);
+      for (int i = 0; i < n; i++) {  /* row sums of the first delta, from scratch */
+        v[i] = qc_zero();
+        for (int j = 0; j < n; j++) {
+          int negative = (j > 0) && ((code >> (j - 1)) & 1);
+          v[i] = negative ? qc_sub(v[i], load_entry(A, n, i, j)) : qc_add(v[i], load_entry(A, n, i, j));
+        }
+      }
+      for (uint64_t k = start; k < end; k++) {
+        qc_t prod = qc_one();
+        for (int i = 0; i < n; i++) prod = qc_mul(prod, v[i]);
+        acc = (popcount64(code) & 1) ? qc_sub(acc, prod) : qc_add(acc, prod);
+        if (k + 1 == end) break;
+        int b = __builtin_ctzll(k + 1);   /* the one sign that changes */
+        code ^= 1ull << b;
+        int now_negative = (code >> b) & 1;
+        for (int i = 0; i < n; i++) {
+          qc_t a2 = load_entry(A, n, i, b + 1);
+          a2.re = a2.re + a2.re;
+          a2.im = a2.im + a2.im;
+          v[i] = now_negative ? qc_sub(v[i], a2) : qc_add(v[i], a2);
+        }
+      }
+    }
+    free(v);
+    part[rank] = acc;
+  }
+  qc_t sum = qc_zero();
+  for (int r = 0; r < P; r++) sum = qc_add(sum, part[r]);
+  free(part);
+  if (fail) return -1;
+  q_t scale = (q_t)1;
+  for (int i = 0; i < n - 1; i++) scale = scale / (q_t)2;
+  sum.re *= scale;
+  sum.im *= scale;
+  store_result(sum, out4);
   return 0;
 }
 

@@ -1,0 +1,90 @@
+"""Multi-GPU sharding of one large permanent over the Gray index range.
+
+The split is Algorithm 2's (and Algorithm 1's) of arXiv 1606.05836: each rank
+takes one contiguous range of the iteration index, here of the Gray index
+[0, 2^M) (Glynn M = n-1, Ryser M = n), with lengths differing by at most one.
+Each rank computes its un-normalised double-double partial sum on its own GPU
+(``perm_glynn_range`` / ``perm_ryser_range``), and the one exchange of the method
+— the paper's final MPI reduce of the per-process sums — is an all-gather of the
+32-byte partials, summed in rank order on every rank (deterministic), then scaled
+(Glynn: / 2^(n-1); Ryser: x (-1)^n).
+"""
+from __future__ import annotations
+
+import torch
+
+
+def shard_range(total: int, rank: int, world: int) -> tuple[int, int]:
+    """Contiguous [begin, end) of ``total`` indices for ``rank`` of ``world``."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("bad rank/world")
+    q, r = divmod(total, world)
+    begin = rank * q + min(rank, r)
+    return begin, begin + q + (1 if rank < r else 0)
+
+
+def two_sum(a: float, b: float) -> tuple[float, float]:
+    s = a + b
+    bb = s - a
+    return s, (a - (s - bb)) + (b - bb)
+
+
+def dd_sum(pairs) -> tuple[float, float]:
+    """Sum of (hi, lo) double-double values in the given order."""
+    hi, lo = 0.0, 0.0
+    for h, l in pairs:
+        s, e = two_sum(hi, h)
+        e += lo + l
+        hi, lo = two_sum(s, e)
+    return hi, lo
+
+
+def exchange_partials(part: tuple[complex, complex], group=None) -> tuple[complex, complex]:
+    """All-gather every rank's (hi, lo) complex partial and sum them in rank order."""
+    import torch.distributed as dist
+
+    world = dist.get_world_size(group)
+    backend = dist.get_backend(group)
+    dev = torch.device("cuda", torch.cuda.current_device()) if backend == "nccl" else torch.device("cpu")
+    mine = torch.tensor([part[0].real, part[0].imag, part[1].real, part[1].imag], dtype=torch.float64, device=dev)
+    bufs = [torch.empty_like(mine) for _ in range(world)]
+    dist.all_gather(bufs, mine, group=group)
+    vals = [b.cpu().tolist() for b in bufs]
+    re = dd_sum((v[0], v[2]) for v in vals)
+    im = dd_sum((v[1], v[3]) for v in vals)
+    return complex(re[0], im[0]), complex(re[1], im[1])
+
+
+def sharded_permanent(n: int, method: str, partial_fn, rank: int, world: int, group=None) -> complex:
+    """Per(A) from per-rank Gray-range partials.
+
+    partial_fn(k_begin, k_end) -> (hi, lo) must return this rank's un-normalised
+    partial sum (e.g. a closure over ``paper_1606_05836_gb300.glynn_range`` on this
+    rank's GPU).  With world == 1 no collective is used.
+    """
+    if n == 0:
+        return 1.0 + 0.0j
+    M = n - 1 if method == "glynn" else n
+    kb, ke = shard_range(1 << M, rank, world)
+    part = partial_fn(kb, ke)
+    if world > 1:
+        hi, lo = exchange_partials(part, group)
+    else:
+        hi, lo = part
+    total = complex(hi.real + lo.real, hi.imag + lo.imag)
+    if method == "glynn":
+        return total / float(1 << (n - 1))
+    return -total if n & 1 else total
+
+
+def gpu_partial_fn(A: torch.Tensor, method: str = "glynn", **opts):
+    """partial_fn for sharded_permanent running the GPU range kernel on A's device."""
+    from . import glynn_range, ryser_range
+
+    f = glynn_range if method == "glynn" else ryser_range
+
+    def run(kb: int, ke: int):
+        r = f(A, kb, ke, **opts).cpu()
+        return complex(r[0].item()), complex(r[1].item())
+
+    return run

@@ -342,3 +342,25 @@ def test_prob_orientation_rows_are_inputs():
     assert per.rel_err(sub[0, 0] * sub[1, 1] + sub[0, 1] * sub[1, 0]) < 1e-14
     p_t, _ = oracle.prob(U.T, t, s)
     assert p == pytest.approx(p_t, rel=1e-13)
+
+
+# --------------------------------------------------------------------------
+# Gray-order quad Glynn (the O(n 2^n) evaluation used for larger references)
+# --------------------------------------------------------------------------
+
+def test_glynn_gray_pins():
+    # closed forms of the paper's all-r tables and a diagonal
+    A = S.all_r(18, 0.2)
+    assert oracle.glynn_gray(A).rel_err(closed_allr(18, 0.2)) < 1e-14
+    d = S.circular_gaussian((13,), 6)
+    assert oracle.glynn_gray(S.diagonal(d)).rel_err(np.prod(d)) < 1e-14
+    # the derangement number of the worked example, exactly
+    assert oracle.glynn_gray(S.ones_minus_identity(12)).hi == 176214841
+    # agreement with the direct-sum evaluation far below FP64 rounding, any thread split
+    B = S.gaussian(15, 7, 1.0)
+    ref = oracle.glynn(B)
+    for threads in (1, 3, 8):
+        assert qrel(ref, oracle.glynn_gray(B, threads=threads)) < 1e-28
+    # exact integer counts of 0/1 matrices
+    C = S.bernoulli01(16, 9)
+    assert oracle.glynn_gray(C.astype(np.complex128)).hi == oracle.ryser_int(C)

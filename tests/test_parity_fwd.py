@@ -192,3 +192,26 @@ def test_precision_gap_allones_matches_paper(pg):
     for n in (28, 30, 32):
         eg, er = results[n]
         assert er > 1e5 * max(eg, 1e-16)
+
+
+def _block_diag_case(n, seed):
+    h = n // 2
+    B1, B2 = S.gaussian(h, seed), S.gaussian(n - h, seed + 1)
+    A = np.zeros((n, n), dtype=np.complex128)
+    A[:h, :h], A[h:, h:] = B1, B2
+    P, Q = S.random_permutations(n, seed + 2)
+    return A[P][:, Q], oracle.glynn(B1).hi * oracle.glynn(B2).hi
+
+
+def test_block_diagonal_n36(pg):
+    A, want = _block_diag_case(36, 36036)
+    assert rel(val(pg.glynn(to_dev(A))), want) < REL_TOL
+
+
+@pytest.mark.slow
+def test_block_diagonal_n40_full_size(pg):
+    """n = 40, the largest size of the sweep (2^39 Gray terms, ~3.5 min on one
+    GB300): Per of a permuted block-diagonal matrix = product of its two n = 20
+    block permanents from the quad oracle."""
+    A, want = _block_diag_case(40, 40040)
+    assert rel(val(pg.glynn(to_dev(A))), want) < REL_TOL

@@ -1,0 +1,72 @@
+"""The precision ladder (FP64 / FP64 + double-double accumulation / FP32 products
+with compensated accumulation) against stored oracle references, and the paper's
+Ryser-vs-BB/FG precision finding on cancellation-heavy input.
+
+References: tests/golden/ladder_refs.tsv, written by make_ladder_refs.py from the
+quad Gray-order Glynn oracle (complex inputs) and the exact int128 Ryser oracle
+(0/1 inputs).
+"""
+import importlib.util
+import os
+
+import pytest
+
+from conftest import GOLDEN, read_tsv
+from gpu_util import REL_TOL, to_dev, val
+
+pytestmark = pytest.mark.gpu
+
+_spec = importlib.util.spec_from_file_location("make_ladder_refs", os.path.join(GOLDEN, "make_ladder_refs.py"))
+refs_mod = importlib.util.module_from_spec(_spec)
+_spec.loader.exec_module(refs_mod)
+
+
+@pytest.fixture(scope="module")
+def pg():
+    import paper_1606_05836_gb300 as pg
+    from paper_1606_05836_gb300 import build
+    build.build()
+    pg.library()
+    return pg
+
+
+def ladder_errors(pg):
+    out = []
+    for row in read_tsv("ladder_refs.tsv"):
+        n, seed = int(row["n"]), int(row["seed"])
+        A = refs_mod.make_input(row["kind"], n, seed)
+        assert refs_mod.digest(A) == row["sha"], "regenerated input differs from the stored reference's input"
+        want_hi = complex(float(row["re_hi"]), float(row["im_hi"]))
+        want_lo = complex(float(row["re_lo"]), float(row["im_lo"]))
+        dA = to_dev(A)
+        errs = {}
+        for method, f in (("glynn", pg.glynn), ("ryser", pg.ryser)):
+            for prec in ("fp64", "fp64_dd", "fp32p_dd"):
+                got = val(f(dA, prec=prec))
+                errs[(method, prec)] = abs((got - want_hi) - want_lo) / abs(want_hi)
+        out.append((row["kind"], n, errs))
+    return out
+
+
+def test_precision_ladder(pg):
+    results = ladder_errors(pg)
+    print()
+    print("%-11s %3s  %-9s %-9s %-9s | %-9s %-9s %-9s" % ("input", "n", "G fp64", "G dd", "G fp32p", "R fp64",
+                                                           "R dd", "R fp32p"))
+    for kind, n, e in results:
+        print("%-11s %3d  %.2e  %.2e  %.2e  | %.2e  %.2e  %.2e" % (
+            kind, n, e[("glynn", "fp64")], e[("glynn", "fp64_dd")], e[("glynn", "fp32p_dd")],
+            e[("ryser", "fp64")], e[("ryser", "fp64_dd")], e[("ryser", "fp32p_dd")]))
+    for kind, n, e in results:
+        # FP64 Glynn meets the 1e-10 bar on every input, with or without compensation
+        assert e[("glynn", "fp64")] < REL_TOL, (kind, n)
+        assert e[("glynn", "fp64_dd")] < REL_TOL, (kind, n)
+        # compensated accumulation is never materially worse than plain
+        assert e[("glynn", "fp64_dd")] <= 4 * e[("glynn", "fp64")] + 1e-15, (kind, n)
+        # the FP32-product rung has its own, stated error
+        assert e[("glynn", "fp32p_dd")] < 1e-3, (kind, n)
+    # the paper's finding: on cancellation-heavy input Ryser in FP64 loses many
+    # more digits than BB/FG (its "special-derived" matrices; all-ones errors
+    # 10^7-10^9 apart)
+    big = [e for kind, n, e in results if kind == "ones_noise" and n == 28][0]
+    assert big[("ryser", "fp64")] > 1e3 * max(big[("glynn", "fp64")], 1e-16)

@@ -1,0 +1,94 @@
+"""Sharding of one permanent over ranks (the Gray-range split of Algorithms 1/2
+and the final reduce of the per-rank sums), tested on CPU with gloo ranks and
+the oracle computing each rank's partial; and on one GPU as K logical shards."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+import oracle
+import synthetic as S
+from paper_1606_05836_gb300.shard import dd_sum, shard_range, sharded_permanent
+
+
+def test_shard_range_partitions_exactly():
+    for total in (0, 1, 7, 1 << 20, (1 << 39) + 5):
+        for world in (1, 2, 3, 8, 13):
+            ranges = [shard_range(total, r, world) for r in range(world)]
+            assert ranges[0][0] == 0 and ranges[-1][1] == total
+            for (a, b), (c, d) in zip(ranges, ranges[1:]):
+                assert b == c
+            lens = [b - a for a, b in ranges]
+            assert max(lens) - min(lens) <= 1
+
+
+def test_dd_sum_is_exact_for_cancelling_parts():
+    parts = [(1e16, 1.0), (-1e16, 0.5), (3.0, 0.0)]
+    hi, lo = dd_sum(parts)
+    assert hi + lo == 4.5
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank_main(rank, world, port, n, method, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    A = S.gaussian(n, 77)
+    f = oracle.glynn_range if method == "glynn" else oracle.ryser_range
+
+    def partial(kb, ke):
+        r = f(A, kb, ke, gray=True, threads=1)
+        return r.hi, r.lo
+
+    per = sharded_permanent(n, method, partial, rank, world)
+    q.put((rank, per))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("method", ["glynn", "ryser"])
+def test_gloo_two_ranks_equal_the_full_sum(method):
+    n, world = 11, 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, n, method, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    got = dict(q.get(timeout=10) for _ in range(world))
+    want = oracle.ryser(S.gaussian(n, 77))
+    for r in range(world):
+        assert want.rel_err(got[r]) < 1e-14
+    assert got[0] == got[1]  # every rank sums the gathered partials in the same order
+
+
+@pytest.mark.gpu
+def test_logical_shards_on_one_gpu():
+    """K logical shards (disjoint Gray ranges on one GPU) add up to the single launch."""
+    import torch
+    import paper_1606_05836_gb300 as pg
+    from paper_1606_05836_gb300.shard import gpu_partial_fn
+    A = S.gaussian(26, 88)
+    dA = torch.as_tensor(A).cuda()
+    full = complex(pg.glynn(dA).cpu().item())
+    fn = gpu_partial_fn(dA, "glynn")
+    K = 5
+    parts = [fn(*shard_range(1 << 25, r, K)) for r in range(K)]
+    re = dd_sum((p[0].real, p[1].real) for p in parts)
+    im = dd_sum((p[0].imag, p[1].imag) for p in parts)
+    per = complex(re[0] + re[1], im[0] + im[1]) / float(1 << 25)
+    assert abs(per - full) <= 1e-12 * abs(full)
+    assert abs(sharded_permanent(26, "glynn", fn, 0, 1) - full) <= 1e-12 * abs(full)
