@@ -14,7 +14,7 @@ __global__ void __launch_bounds__(256) grad_reduce_kernel(GradReduceArgs r) {
   const int ij = blockIdx.x;
   const int i = ij / n, j = ij % n;
   __shared__ dd red[2][8];
-  const double2* base = r.state + (long long)((i * n + j) * 2) * r.P;
+  const double2* base = r.state + (long long)(i * n + j) * r.P;
   dd tr{0.0, 0.0}, ti{0.0, 0.0};
   for (long long T = threadIdx.x; T < r.P; T += blockDim.x) {
     const double2 v = base[T];
@@ -134,7 +134,7 @@ int grad_layout(int n, const perm_opts* o, GradLayout* L) {
   L->partials = off;
   off = align256(off + 32 * (size_t)grid);
   L->state = off;
-  off = align256(off + sizeof(double2) * 2 * (size_t)n * n * (size_t)L->P);
+  off = align256(off + sizeof(double2) * (size_t)n * n * (size_t)L->P);
   L->total = off;
   return PERM_OK;
 }

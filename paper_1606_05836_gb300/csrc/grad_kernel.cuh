@@ -5,11 +5,11 @@
 // suffix pass (stored per lane in shared memory) and one prefix pass — 3(n-2)
 // complex multiplies, no division (a row sum may be exactly zero).  With
 // w_i = (prod delta) q_i, G_ij = sum over terms of w_i delta_j is accumulated at
-// O(n) per term: S_i = running sum of w_i (shared memory), and only when the Gray
-// code flips column j is G_:j += delta_j^old (S - snap_:j), snap_:j = S
-// (delta_j is constant between its flips).  The per-lane G and snap (n x n each)
-// live in the caller's workspace, lane-interleaved so every warp access is
-// coalesced; a second kernel sums the lanes in a fixed order.
+// O(n) per term: S_i = running sum of w_i (shared memory) and H_ij = G_ij -
+// delta_j S_i, which changes only when the Gray code flips column j
+// (delta_j -> -delta_j): H_:j += 2 delta_j^old S.  At the end G = H + delta S.
+// The per-lane H (n x n) lives in the caller's workspace, lane-interleaved so
+// every warp access is coalesced; a second kernel sums the lanes in a fixed order.
 #pragma once
 #include "fwd_kernel.cuh"
 
@@ -24,33 +24,61 @@ struct GradArgs {
   int chunk_log2;
   uint64_t per_q, per_r;  // floor/ceil split of the 2^(n-1) Gray indices over the lanes
   double neg_zero;
-  double2* state;         // [(i*N + j)*2 + {0: G, 1: snap}][P]
+  double2* state;         // H: [i*N + j][P]
   long long P;            // lanes in the grid (= state stride)
   double* partials;       // forward Per: 4 doubles per block
   int* scale_exp;         // [1 + N]: sum_i s_i, then s_i (written by block 0)
 };
 
+// Like stage_matrix, but stores column 0 and the doubled columns 2 a_{:,b+1}
+// only (rows scaled by 2^{s_i}).  Returns sum_i s_i.
 template <int N>
-__device__ __forceinline__ double2* gstate(const GradArgs& a, int i, int j, int w, long long T) {
-  return a.state + ((long long)((i * N + j) * 2 + w)) * a.P + T;
+__device__ int stage_matrix_doubled(const double2* __restrict__ A, int lda, double2* Col0, double2* Step,
+                                    int* s_row) {
+  constexpr int NP = Stride<N>::value;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    double nrm = 0.0;
+    for (int j = 0; j < N; j++) {
+      const double2 v = A[(size_t)i * lda + j];
+      nrm = fma(v.x, v.x, nrm);
+      nrm = fma(v.y, v.y, nrm);
+    }
+    const int e2 = (int)((__double2hiint(nrm) >> 20) & 0x7FF) - 1023;
+    int s = (nrm == 0.0) ? 0 : -(e2 >> 1);
+    s = s > 1000 ? 1000 : (s < -1000 ? -1000 : s);
+    s_row[i] = s;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    const int i = idx / N, j = idx % N;
+    const double f = pow2_double(s_row[i]);
+    const double2 v = A[(size_t)i * lda + j];
+    if (j == 0) Col0[i] = make_double2(v.x * f, v.y * f);
+    else Step[(j - 1) * NP + i] = make_double2(2.0 * (v.x * f), 2.0 * (v.y * f));
+  }
+  int total = 0;
+  for (int i = 0; i < N; i++) total += s_row[i];
+  __syncthreads();
+  return total;
 }
 
-// G_:j += delta (S - snap_:j); snap_:j = S   (delta = +-1 as a sign mask)
 template <int N>
-__device__ __forceinline__ void flush_column(const GradArgs& a, int j, unsigned long long neg_mask,
-                                             const double2* S, int B, long long T) {
-  const double sgn = xor_sign(1.0, neg_mask);
+__device__ __forceinline__ double2* hstate(const GradArgs& a, int i, int j, long long T) {
+  return a.state + (long long)(i * N + j) * a.P + T;
+}
+
+// H_:j += f S   (f = +-2 as a double: 2 delta_j^old at a flip, delta_j at the end)
+template <int N>
+__device__ __forceinline__ void flush_column(const GradArgs& a, int j, double f, const double2* S, int B,
+                                             long long T) {
 #pragma unroll 8
   for (int i = 0; i < N; i++) {
     const double2 s = S[i * B];
-    double2* gp = gstate<N>(a, i, j, 0, T);
-    double2* sp = gstate<N>(a, i, j, 1, T);
-    const double2 snap = *sp;
-    double2 g = *gp;
-    g.x = fma(sgn, s.x - snap.x, g.x);
-    g.y = fma(sgn, s.y - snap.y, g.y);
-    *gp = g;
-    *sp = s;
+    double2* hp = hstate<N>(a, i, j, T);
+    double2 h = *hp;
+    h.x = fma(f, s.x, h.x);
+    h.y = fma(f, s.y, h.y);
+    *hp = h;
   }
 }
 
@@ -58,15 +86,17 @@ template <int N>
 __global__ void __launch_bounds__(GRAD_BLOCK, 1) grad_kernel(GradArgs a) {
   extern __shared__ double2 smem[];
   constexpr int NP = Stride<N>::value;
-  double2* Acol = smem;
-  double2* Step = smem + N * NP;
+  // column 0 of A, then the doubled columns 2 a_{:,b+1} (b = 0..N-2); the row
+  // sums at a chunk start are (2 a_{:,0} + sum_b +-2 a_{:,b+1}) / 2, exact.
+  double2* Col0 = smem;
+  double2* Step = smem + NP;
   const int B = blockDim.x;
-  double2* suf = smem + 2 * N * NP + threadIdx.x;        // suf[i * B]
-  double2* S = smem + 2 * N * NP + N * B + threadIdx.x;  // S[i * B]
+  double2* suf = smem + N * NP + threadIdx.x;            // suf[i * B]
+  double2* S = smem + N * NP + N * B + threadIdx.x;      // S[i * B]
   __shared__ int s_row[N];
   __shared__ dd wsum[2][GRAD_BLOCK / 32];
 
-  const int scale_exp = stage_matrix<N>(a.A, a.lda, KIND_GLYNN, Acol, Step, s_row);
+  const int scale_exp = stage_matrix_doubled<N>(a.A, a.lda, Col0, Step, s_row);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.scale_exp[0] = scale_exp;
     for (int i = 0; i < N; i++) a.scale_exp[1 + i] = s_row[i];
@@ -80,10 +110,7 @@ __global__ void __launch_bounds__(GRAD_BLOCK, 1) grad_kernel(GradArgs a) {
   // per-lane state starts at zero
   for (int i = 0; i < N; i++) {
     S[i * B] = make_double2(0.0, 0.0);
-    for (int j = 0; j < N; j++) {
-      *gstate<N>(a, i, j, 0, T) = make_double2(0.0, 0.0);
-      *gstate<N>(a, i, j, 1, T) = make_double2(0.0, 0.0);
-    }
+    for (int j = 0; j < N; j++) *hstate<N>(a, i, j, T) = make_double2(0.0, 0.0);
   }
 
   double ar = 0.0, ai = 0.0;
@@ -97,16 +124,27 @@ __global__ void __launch_bounds__(GRAD_BLOCK, 1) grad_kernel(GradArgs a) {
       vr[i] = 0.0;
       vi[i] = 0.0;
     }
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      const double2 x = Col0[i];
+      vr[i] = x.x + x.x;
+      vi[i] = x.y + x.y;
+    }
 #pragma unroll 1
-    for (int j = 0; j < N; j++) {
-      const double coef = (j == 0) ? 1.0 : (((g >> (j - 1)) & 1ull) ? -1.0 : 1.0);
-      const double2* col = Acol + j * NP;
+    for (int b = 0; b < N - 1; b++) {
+      const double coef = ((g >> b) & 1ull) ? -1.0 : 1.0;
+      const double2* col = Step + b * NP;
 #pragma unroll
       for (int i = 0; i < N; i++) {
         const double2 x = col[i];
         vr[i] = fma(coef, x.x, vr[i]);
         vi[i] = fma(coef, x.y, vi[i]);
       }
+    }
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      vr[i] *= 0.5;
+      vi[i] *= 0.5;
     }
 #pragma unroll 1
     while (true) {
@@ -162,10 +200,9 @@ __global__ void __launch_bounds__(GRAD_BLOCK, 1) grad_kernel(GradArgs a) {
       }
       ++k;
       if (k >= ke) break;
-      // column j = b+1 flips: flush its segment with its old sign, then step
+      // column j = b+1 flips (delta_j -> -delta_j): H_:j += 2 delta_j^old S
       const int b = __ffsll((long long)k) - 1;
-      const unsigned long long old_neg = ((g >> b) & 1ull) << 63;
-      flush_column<N>(a, b + 1, old_neg, S, B, T);
+      flush_column<N>(a, b + 1, xor_sign(2.0, ((g >> b) & 1ull) << 63), S, B, T);
       g ^= 1ull << b;
       if (k >= c1) break;  // next chunk: recompute the row sums from g
       // bit now set: delta_{b+2} became -1, subtract 2a; bit now clear: add
@@ -179,10 +216,10 @@ __global__ void __launch_bounds__(GRAD_BLOCK, 1) grad_kernel(GradArgs a) {
       }
     }
   }
-  // final flush of every column with its current sign (column 0 is always +1)
+  // G = H + delta S with every column's current sign (column 0 is always +1)
   for (int j = 0; j < N; j++) {
     const unsigned long long neg = (j == 0) ? 0ull : (((g >> (j - 1)) & 1ull) << 63);
-    flush_column<N>(a, j, neg, S, B, T);
+    flush_column<N>(a, j, xor_sign(1.0, neg), S, B, T);
   }
 
   // forward permanent: block partials (the reduce kernel sums them in order)
@@ -227,7 +264,7 @@ template <int N>
 int grad_blocks_per_sm(int* out);
 
 inline size_t grad_smem_bytes(int N) {
-  return (size_t)2 * N * (N | 1) * sizeof(double2) + (size_t)2 * N * GRAD_BLOCK * sizeof(double2);
+  return (size_t)N * (N | 1) * sizeof(double2) + (size_t)2 * N * GRAD_BLOCK * sizeof(double2);
 }
 
 }  // namespace permk
