@@ -91,6 +91,14 @@ int perm_glynn(const perm_c128* dA, int n, int lda, perm_c128* dOut, void* dWork
 int perm_ryser(const perm_c128* dA, int n, int lda, perm_c128* dOut, void* dWork, size_t workBytes,
                const perm_opts* opts, void* stream);
 
+/* Per(A) by Ryser's formula halved to 2^(n-1) subsets (Nijenhuis and Wilf):
+ * Per = (-1)^(n-1) 2 sum_{S in [n-1]} (-1)^|S| prod_i (x_i + sum_{j in S} a_ij),
+ * x_i = a_{i,n} - (1/2) sum_j a_ij — Eq. (S1) with the same term count as Eq.
+ * (S2).  The paper runs only the plain 2^n-subset form; this variant is here for
+ * its summation-order and precision comparison.  dOut receives one perm_c128. */
+int perm_ryser_nw(const perm_c128* dA, int n, int lda, perm_c128* dOut, void* dWork, size_t workBytes,
+                  const perm_opts* opts, void* stream);
+
 /* Partial sums over Gray indices [k_begin, k_end) — the index-range split of
  * Algorithms 1 and 2 (each MPI process took such a range) and the unit a
  * multi-GPU shard computes.  The sum is of the un-normalised signed terms

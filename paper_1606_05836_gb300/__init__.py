@@ -9,6 +9,7 @@ Functions mirror the C entry points:
 
 * :func:`glynn`  -- Per(A), BB/FG formula (Supp. Eq. (S2), Algorithm 2 of arXiv 1606.05836)
 * :func:`ryser`  -- Per(A), Ryser formula (Supp. Eq. (S1), Algorithm 1)
+* :func:`ryser_nw` -- Per(A), Ryser's formula halved to 2^(n-1) subsets
 * :func:`glynn_range`, :func:`ryser_range` -- partial sums over a Gray-index range
 * :func:`batched`, :class:`BatchedPermanents` -- many permanents of mixed sizes in
   one persistent launch (CUDA-graph capture, autotuned launch shape)
@@ -25,7 +26,7 @@ import torch
 from . import _native
 from ._native import PERM_MAX_N, PRECISIONS, Opts, PermError
 
-__all__ = ["glynn", "ryser", "glynn_range", "ryser_range", "workspace_size", "PermError", "PERM_MAX_N",
+__all__ = ["glynn", "ryser", "ryser_nw", "glynn_range", "ryser_range", "workspace_size", "PermError", "PERM_MAX_N",
            "PRECISIONS", "library", "batched", "BatchedPermanents", "grad", "PermAbs2", "prob"]
 
 _workspaces: dict = {}
@@ -131,6 +132,11 @@ def prob(U: torch.Tensor, s, t, prec="fp64", chunk_log2=0, block=0, grid=0):
                              nbytes, ctypes.byref(o), ctypes.c_void_p(_stream_ptr(dev)))
     _native.check(st, "prob_sample")
     return p.value, complex(per[0], per[1])
+
+
+def ryser_nw(A: torch.Tensor, prec="fp64", chunk_log2=0, block=0, grid=0) -> torch.Tensor:
+    """Per(A) by Ryser's formula over 2^(n-1) subsets (Nijenhuis-Wilf form); 0-dim complex128."""
+    return _run("perm_ryser_nw", A, (), 1, prec=prec, chunk_log2=chunk_log2, block=block, grid=grid)[0]
 
 
 def _range(fname, A, k_begin, k_end, **opts):

@@ -20,6 +20,7 @@ EXPORTS = (
     "perm_workspace_size",
     "perm_glynn",
     "perm_ryser",
+    "perm_ryser_nw",
     "perm_glynn_range",
     "perm_ryser_range",
     "perm_batched_workspace_size",
@@ -66,7 +67,7 @@ def load(path: str | None = None):
     op = ctypes.POINTER(Opts)
     lib.perm_workspace_size.argtypes = [i32, op]
     lib.perm_workspace_size.restype = sz
-    for f in ("perm_glynn", "perm_ryser"):
+    for f in ("perm_glynn", "perm_ryser", "perm_ryser_nw"):
         getattr(lib, f).argtypes = [vp, i32, i32, vp, vp, sz, op, vp]
         getattr(lib, f).restype = i32
     for f in ("perm_glynn_range", "perm_ryser_range"):

@@ -13,7 +13,14 @@
 
 namespace permk {
 
-enum { KIND_GLYNN = 0, KIND_RYSER = 1 };
+// KIND_RYSER_NW: Ryser's formula over the 2^(n-1) subsets of the first n-1
+// columns, Per = (-1)^(n-1) 2 sum_S (-1)^|S| prod_i (x_i + sum_{j in S} a_ij),
+// x_i = a_{i,n-1} - (1/2) sum_j a_ij (Nijenhuis and Wilf's halving of Eq. (S1)).
+// KIND_GLYNN_BASE: Eq. (S2) for a matrix with repeated columns, one term class of
+// the multiplicity expansion: v_i = x_i + sum_{j in F} delta_j a_ij over the
+// free (non-repeated) columns F, x = a fixed combination of the repeated
+// columns (base vector Xb), delta_j = -1 iff bit j of g(k) is set.
+enum { KIND_GLYNN = 0, KIND_RYSER = 1, KIND_RYSER_NW = 2, KIND_GLYNN_BASE = 3 };
 
 // ---------------------------------------------------------------------------
 // small helpers (integer-pipe sign handling, double-double)
@@ -169,29 +176,45 @@ __device__ __forceinline__ double2 ldcol(const double2* p) {
 }
 
 // Walks Gray indices [kb, ke): at every chunk start (every CH steps from kb) the
-// row sums are recomputed exactly from the columns Acol (v_i = sum_j coef_j a_ij,
-// Glynn: coef_0 = +1 and coef_{b+1} = -1 iff bit b of g(k) is set; Ryser:
-// coef_b = [bit b of g(k)]); every other step adds +-Step[b], b = ctz(k).
-// Columns are `stride` complex numbers apart.  GLOBAL selects read-only global
-// loads instead of shared-memory loads.
+// row sums are recomputed exactly from the columns Acol (v_i = base_i + sum_j
+// coef_j a_ij; Glynn: base 0, coef_0 = +1 and coef_{b+1} = -1 iff bit b of g(k)
+// is set; Ryser: base 0, coef_b = [bit b of g(k)]; Ryser-NW: base x_i (the
+// vector Xb), coef_b = [bit b] over the first n-1 columns); every other step
+// adds +-Step[b], b = ctz(k).  Columns are `stride` complex numbers apart.
+// GLOBAL selects read-only global loads instead of shared-memory loads.
 template <int N, int PREC, int TUNE, bool GLOBAL>
 __device__ __forceinline__ void walk_range(const double2* __restrict__ Acol, const double2* __restrict__ Step,
-                                           int stride, bool glynn, uint64_t kb, uint64_t ke, uint64_t CH, double nz,
-                                           double& ar, double& ai, double& cr, double& ci) {
+                                           const double2* __restrict__ Xb, int stride, int kind, int base_cols,
+                                           uint64_t kb, uint64_t ke, uint64_t CH, double nz, double& ar, double& ai,
+                                           double& cr, double& ci) {
+  const bool glynn = (kind == KIND_GLYNN);
+  const bool glynn_signs = glynn || kind == KIND_GLYNN_BASE;
+  const bool has_base = (kind == KIND_RYSER_NW || kind == KIND_GLYNN_BASE);
   // Glynn: a set Gray bit means delta = -1 (subtract 2a when it turns on);
   // Ryser: a set bit means the column is in S (add a when it turns on).
-  const unsigned long long on_mask = glynn ? 0x8000000000000000ull : 0ull;
+  const unsigned long long on_mask = glynn_signs ? 0x8000000000000000ull : 0ull;
+  const int ncols = (kind == KIND_RYSER_NW) ? N - 1 : (kind == KIND_GLYNN_BASE ? base_cols : N);
   for (uint64_t c0 = kb; c0 < ke; c0 += CH) {
     const uint64_t c1 = (ke - c0 > CH) ? c0 + CH : ke;
     uint64_t g = c0 ^ (c0 >> 1);
     double vr[N], vi[N];
-    // exact row sums at the chunk start: v_i = sum_j coef_j a_ij
+    // exact row sums at the chunk start: v_i = base_i + sum_j coef_j a_ij
+    if (has_base) {
 #pragma unroll
-    for (int i = 0; i < N; i++) { vr[i] = 0.0; vi[i] = 0.0; }
+      for (int i = 0; i < N; i++) {
+        const double2 x = ldcol<GLOBAL>(Xb + i);
+        vr[i] = x.x;
+        vi[i] = x.y;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < N; i++) { vr[i] = 0.0; vi[i] = 0.0; }
+    }
 #pragma unroll 1
-    for (int j = 0; j < N; j++) {
+    for (int j = 0; j < ncols; j++) {
       double coef;
       if (glynn) coef = (j == 0) ? 1.0 : (((g >> (j - 1)) & 1ull) ? -1.0 : 1.0);
+      else if (kind == KIND_GLYNN_BASE) coef = ((g >> j) & 1ull) ? -1.0 : 1.0;
       else coef = ((g >> j) & 1ull) ? 1.0 : 0.0;
       const double2* col = Acol + j * stride;
 #pragma unroll

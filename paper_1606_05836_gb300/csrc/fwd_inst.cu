@@ -19,7 +19,7 @@ static int launch_one(const FwdArgs& a, int grid, int block, cudaStream_t s) {
   const size_t smem = fwd_smem_bytes(N, a.kind);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(fwd_kernel<N, PREC, TUNE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)fwd_smem_bytes(N, KIND_GLYNN));
+                                         (int)fwd_smem_bytes(N, KIND_GLYNN_BASE));
     if (e != cudaSuccess) return (int)e;
   }
   fwd_kernel<N, PREC, TUNE><<<grid, block, smem, s>>>(a);
@@ -31,7 +31,7 @@ static int occupancy_one(int block, int kind, int* out) {
   const size_t smem = fwd_smem_bytes(N, kind);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(fwd_kernel<N, PREC, TUNE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)fwd_smem_bytes(N, KIND_GLYNN));
+                                         (int)fwd_smem_bytes(N, KIND_GLYNN_BASE));
     if (e != cudaSuccess) return (int)e;
   }
   return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, fwd_kernel<N, PREC, TUNE>, block, smem);

@@ -30,6 +30,15 @@ struct FwdArgs {
   unsigned* ticket; // zero before launch; reset to zero by the last block
   double2* out;     // raw == 0: one value, the permanent; raw == 1: (hi, lo) partial sum
   int raw;
+  // KIND_GLYNN_BASE only: A holds the g distinct columns (n x g, lda); column c is
+  // free column role[c] >= 0, part of the base vector with coefficient coef[c]
+  // (role -2), or the fixed delta = +1 singleton (role -1).  The raw partial sum
+  // is multiplied by `weight`.
+  int g;
+  int nfree;
+  double weight;
+  signed char role[48];
+  short coef[48];
 };
 
 // ---------------------------------------------------------------------------
@@ -50,7 +59,7 @@ struct Stride {
 // exponent range.  Returns sum_i s_i (identical in every block).
 template <int N>
 __device__ int stage_matrix(const double2* __restrict__ A, int lda, int kind, double2* Acol, double2* Step,
-                            int* s_row) {
+                            int* s_row, double2* Xb = nullptr) {
   const int n = N;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double nrm = 0.0;
@@ -78,9 +87,63 @@ __device__ int stage_matrix(const double2* __restrict__ A, int lda, int kind, do
       const double2 v = Acol[(b + 1) * Stride<N>::value + i];
       Step[b * Stride<N>::value + i] = make_double2(v.x + v.x, v.y + v.y);
     }
+  } else if (kind == KIND_RYSER_NW && Xb != nullptr) {
+    // x_i = a_{i,n-1} - (1/2) sum_j a_ij, summed in column order
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double sr = 0.0, si = 0.0;
+      for (int j = 0; j < n; j++) {
+        const double2 v = Acol[j * Stride<N>::value + i];
+        sr += v.x;
+        si += v.y;
+      }
+      const double2 last = Acol[(n - 1) * Stride<N>::value + i];
+      Xb[i] = make_double2(last.x - 0.5 * sr, last.y - 0.5 * si);
+    }
   }
   int total = 0;
   for (int i = 0; i < n; i++) total += s_row[i];
+  __syncthreads();
+  return total;
+}
+
+// Staging for KIND_GLYNN_BASE: rows scaled by 2^{s_i} from the norms of the g
+// distinct columns; free columns to Acol / Step (doubled); the base vector
+// x_i = sum_{role -2} coef_c b_ic + sum_{role -1} b_ic to Xb.
+template <int N>
+__device__ int stage_matrix_base(const FwdArgs& a, double2* Acol, double2* Step, double2* Xb, int* s_row) {
+  constexpr int NP = Stride<N>::value;
+  const int g = a.g;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    double nrm = 0.0;
+    for (int c = 0; c < g; c++) {
+      const double2 v = a.A[(size_t)i * a.lda + c];
+      nrm = fma(v.x, v.x, nrm);
+      nrm = fma(v.y, v.y, nrm);
+    }
+    const int e2 = (int)((__double2hiint(nrm) >> 20) & 0x7FF) - 1023;
+    int s = (nrm == 0.0) ? 0 : -(e2 >> 1);
+    s = s > 1000 ? 1000 : (s < -1000 ? -1000 : s);
+    s_row[i] = s;
+    const double f = pow2_double(s);
+    double xr = 0.0, xi = 0.0;
+    for (int c = 0; c < g; c++) {
+      const double2 v = a.A[(size_t)i * a.lda + c];
+      const double br = v.x * f, bi = v.y * f;
+      const int role = a.role[c];
+      if (role >= 0) {
+        Acol[role * NP + i] = make_double2(br, bi);
+        Step[role * NP + i] = make_double2(br + br, bi + bi);
+      } else {
+        const double k = (role == -1) ? 1.0 : (double)a.coef[c];
+        xr = fma(k, br, xr);
+        xi = fma(k, bi, xi);
+      }
+    }
+    Xb[i] = make_double2(xr, xi);
+  }
+  __syncthreads();
+  int total = 0;
+  for (int i = 0; i < N; i++) total += s_row[i];
   __syncthreads();
   return total;
 }
@@ -94,10 +157,14 @@ __global__ void __launch_bounds__(256, 1) fwd_kernel(FwdArgs a) {
   extern __shared__ double2 smem[];
   double2* Acol = smem;
   constexpr int NP = Stride<N>::value;
-  double2* Step = (a.kind == KIND_GLYNN) ? smem + N * NP : smem;
+  double2* Step = (a.kind == KIND_GLYNN || a.kind == KIND_GLYNN_BASE) ? smem + N * NP : smem;
+  // base vector: Ryser-NW keeps it in the (unused) second half, the
+  // multiplicity kind after the step columns
+  double2* Xb = (a.kind == KIND_GLYNN_BASE) ? smem + 2 * N * NP : smem + N * NP;
   __shared__ int s_row[N];
 
-  const int scale_exp = stage_matrix<N>(a.A, a.lda, a.kind, Acol, Step, s_row);
+  const int scale_exp = (a.kind == KIND_GLYNN_BASE) ? stage_matrix_base<N>(a, Acol, Step, Xb, s_row)
+                                                    : stage_matrix<N>(a.A, a.lda, a.kind, Acol, Step, s_row, Xb);
   const double nz = a.neg_zero;
 
   const uint64_t T = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -108,7 +175,7 @@ __global__ void __launch_bounds__(256, 1) fwd_kernel(FwdArgs a) {
 
   double ar = 0.0, ai = 0.0, cr = 0.0, ci = 0.0;  // accumulator and (R1/R2) compensation
 
-  walk_range<N, PREC, TUNE, false>(Acol, Step, NP, glynn, kb, ke, CH, nz, ar, ai, cr, ci);
+  walk_range<N, PREC, TUNE, false>(Acol, Step, Xb, NP, a.kind, a.nfree, kb, ke, CH, nz, ar, ai, cr, ci);
 
   // ---- reduction (step a6): warp butterfly, block, last-block grid sum ------
   dd sr, si;
@@ -157,16 +224,21 @@ __global__ void __launch_bounds__(256, 1) fwd_kernel(FwdArgs a) {
     }
     if (lane == 0) {
       // undo the row scaling; Glynn divides by 2^(n-1); Ryser multiplies by (-1)^n
+      // Ryser-NW: x 2 (-1)^(n-1)
       int e = -scale_exp;
       if (!a.raw && glynn) e -= (N - 1);
-      const double neg = (!a.raw && !glynn && (N & 1)) ? -1.0 : 1.0;
+      if (!a.raw && a.kind == KIND_RYSER_NW) e += 1;
+      double neg = 1.0;
+      if (!a.raw && a.kind == KIND_RYSER && (N & 1)) neg = -1.0;
+      if (!a.raw && a.kind == KIND_RYSER_NW && ((N - 1) & 1)) neg = -1.0;
       tr.hi = ldexp(tr.hi, e) * neg;
       tr.lo = ldexp(tr.lo, e) * neg;
       ti.hi = ldexp(ti.hi, e) * neg;
       ti.lo = ldexp(ti.lo, e) * neg;
       if (a.raw) {
-        a.out[0] = make_double2(tr.hi, ti.hi);
-        a.out[1] = make_double2(tr.lo, ti.lo);
+        const double w = (a.kind == KIND_GLYNN_BASE) ? a.weight : 1.0;
+        a.out[0] = make_double2(tr.hi * w, ti.hi * w);
+        a.out[1] = make_double2(tr.lo * w, ti.lo * w);
       } else {
         a.out[0] = make_double2(tr.hi + tr.lo, ti.hi + ti.lo);
       }
@@ -182,7 +254,8 @@ template <int N>
 int fwd_blocks_per_sm(int prec, int tune, int block, int kind, int* out);
 
 inline size_t fwd_smem_bytes(int N, int kind) {
-  return (size_t)(kind == KIND_GLYNN ? 2 : 1) * N * (N | 1) * sizeof(double2);
+  const size_t cols = (kind == KIND_RYSER) ? (size_t)N : (kind == KIND_GLYNN_BASE ? 2 * (size_t)N + 1 : 2 * (size_t)N);
+  return cols * (N | 1) * sizeof(double2);
 }
 
 }  // namespace permk

@@ -146,7 +146,7 @@ int run_fwd(const perm_c128* dA, int n, int lda, int kind, uint64_t k_begin, uin
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PERM_OK : fail_cuda(e);
   }
-  const int M = (kind == permk::KIND_GLYNN) ? n - 1 : n;
+  const int M = (kind == permk::KIND_RYSER) ? n : n - 1;
   const uint64_t full = 1ull << M;
   if (k_begin > k_end || k_end > full) return PERM_ERANGE;
   Plan p;
@@ -232,6 +232,12 @@ int perm_ryser(const perm_c128* dA, int n, int lda, perm_c128* dOut, void* dWork
                const perm_opts* opts, void* stream) {
   const uint64_t full = (n >= 1 && n <= PERM_MAX_N) ? (1ull << n) : 0;
   return run_fwd(dA, n, lda, permk::KIND_RYSER, 0, full, 0, dOut, dWork, workBytes, opts, stream);
+}
+
+int perm_ryser_nw(const perm_c128* dA, int n, int lda, perm_c128* dOut, void* dWork, size_t workBytes,
+                  const perm_opts* opts, void* stream) {
+  const uint64_t full = (n >= 1 && n <= PERM_MAX_N) ? (1ull << (n - 1)) : 0;
+  return run_fwd(dA, n, lda, permk::KIND_RYSER_NW, 0, full, 0, dOut, dWork, workBytes, opts, stream);
 }
 
 int perm_glynn_range(const perm_c128* dA, int n, int lda, uint64_t k_begin, uint64_t k_end, perm_c128* dOut,

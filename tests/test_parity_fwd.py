@@ -215,3 +215,20 @@ def test_block_diagonal_n40_full_size(pg):
     block permanents from the quad oracle."""
     A, want = _block_diag_case(40, 40040)
     assert rel(val(pg.glynn(to_dev(A))), want) < REL_TOL
+
+
+# ------------------------------------------------ Ryser over 2^(n-1) subsets
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 12, 16, 19])
+def test_ryser_nw_vs_oracle(pg, n):
+    A = S.gaussian(n, 700 + n, 1.0)
+    want = oracle.perm_def(A) if n <= 9 else oracle.ryser(A)
+    dA = to_dev(A)
+    for prec, tol in (("fp64", REL_TOL), ("fp64_dd", REL_TOL), ("fp32p_dd", 1e-2)):
+        assert rel(val(pg.ryser_nw(dA, prec=prec)), want) < tol, prec
+    for opts in (dict(grid=3, block=64, chunk_log2=2), dict(chunk_log2=30)):
+        assert rel(val(pg.ryser_nw(dA, **opts)), want) < REL_TOL
+
+
+def test_ryser_nw_fixed_checks(pg):
+    assert val(pg.ryser_nw(to_dev(S.all_r(12, 1.0)))) == 479001600
+    assert val(pg.ryser_nw(to_dev(S.ones_minus_identity(12)))) == 176214841

@@ -40,7 +40,7 @@ def ladder_errors(pg):
         want_lo = complex(float(row["re_lo"]), float(row["im_lo"]))
         dA = to_dev(A)
         errs = {}
-        for method, f in (("glynn", pg.glynn), ("ryser", pg.ryser)):
+        for method, f in (("glynn", pg.glynn), ("ryser", pg.ryser), ("ryser_nw", pg.ryser_nw)):
             for prec in ("fp64", "fp64_dd", "fp32p_dd"):
                 got = val(f(dA, prec=prec))
                 errs[(method, prec)] = abs((got - want_hi) - want_lo) / abs(want_hi)
@@ -51,12 +51,13 @@ def ladder_errors(pg):
 def test_precision_ladder(pg):
     results = ladder_errors(pg)
     print()
-    print("%-11s %3s  %-9s %-9s %-9s | %-9s %-9s %-9s" % ("input", "n", "G fp64", "G dd", "G fp32p", "R fp64",
-                                                           "R dd", "R fp32p"))
+    print("%-11s %3s  %-9s %-9s %-9s | %-9s %-9s %-9s | %-9s %-9s" % (
+        "input", "n", "G fp64", "G dd", "G fp32p", "R fp64", "R dd", "R fp32p", "NW fp64", "NW dd"))
     for kind, n, e in results:
-        print("%-11s %3d  %.2e  %.2e  %.2e  | %.2e  %.2e  %.2e" % (
+        print("%-11s %3d  %.2e  %.2e  %.2e  | %.2e  %.2e  %.2e  | %.2e  %.2e" % (
             kind, n, e[("glynn", "fp64")], e[("glynn", "fp64_dd")], e[("glynn", "fp32p_dd")],
-            e[("ryser", "fp64")], e[("ryser", "fp64_dd")], e[("ryser", "fp32p_dd")]))
+            e[("ryser", "fp64")], e[("ryser", "fp64_dd")], e[("ryser", "fp32p_dd")],
+            e[("ryser_nw", "fp64")], e[("ryser_nw", "fp64_dd")]))
     for kind, n, e in results:
         # FP64 Glynn meets the 1e-10 bar on every input, with or without compensation
         assert e[("glynn", "fp64")] < REL_TOL, (kind, n)
