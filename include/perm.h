@@ -62,7 +62,10 @@ typedef enum {
 typedef enum {
   PERM_FP64 = 0,    /* R0: FP64 products, FP64 accumulation of the terms */
   PERM_FP64_DD = 1, /* R1: FP64 products, double-double accumulation of the terms */
-  PERM_FP32P_DD = 2 /* R2: FP32 n-way products of the FP64 row sums, double-double accumulation */
+  PERM_FP32P_DD = 2, /* R2: FP32 n-way products of the FP64 row sums, double-double accumulation */
+  PERM_FP64_DF = 3   /* R3: the FP64 row sums split exactly into FP32 pairs and multiplied in
+                        double-float arithmetic on the FP32 pipe (~48-bit products), FP64
+                        accumulation; single-permanent entry points only */
 } perm_prec;
 
 /* Launch options; pass NULL for the defaults (every field 0 = default). */
@@ -133,6 +136,25 @@ int perm_batched(const perm_c128* dPacked, const int64_t* dOffsets, const int32_
                  int method, const double* dScale, perm_c128* dOut, double* dProb, void* dWork, size_t workBytes,
                  const perm_opts* opts, void* stream);
 
+/* --- repeated columns (photon collisions) ------------------------------------ */
+
+/* Per(A) of the n x n matrix whose columns are column c of dB repeated
+ * hMult[c] times (c = 0..g-1, sum hMult = n) — the U_ST of Eq. (1) when t_j
+ * photons leave output j.  Eq. (S2) with identical columns grouped: a group of m
+ * copies enters through k = number of its delta signs that are -1, with
+ * binomial weight C(m, k) and row-sum coefficient m - 2k, so the sum has
+ * prod over repeated groups (m_c + 1) x 2^(free columns) terms instead of
+ * 2^(n-1).  One launch walks the (class, free column) index space: each
+ * combination of the repeated groups (a class) is a Gray walk over the free
+ * columns, its sum multiplied by the class weight prod C(m_c, k_c) (-1)^k_c.
+ * dB: device, row-major n x g, ldb >= g.  hMult: host.  dOut: one perm_c128.
+ * Workspace: perm_glynn_mult_workspace_size() bytes, 16-byte aligned.
+ * The paper's runs have no repeated columns; this is the collision case Eq. (1)
+ * allows (t_j > 1). */
+size_t perm_glynn_mult_workspace_size(int n, int g, const int32_t* hMult, const perm_opts* opts);
+int perm_glynn_mult(const perm_c128* dB, int n, int ldb, int g, const int32_t* hMult, perm_c128* dOut, void* dWork,
+                    size_t workBytes, const perm_opts* opts, void* stream);
+
 /* --- one output probability ------------------------------------------------ */
 
 /* Eq. (1) of arXiv 1606.05836 for one input pattern S and output pattern T:
@@ -145,8 +167,10 @@ int perm_batched(const perm_c128* dPacked, const int64_t* dOffsets, const int32_
  *      Aaronson-Arkhipov; this orientation is the one stated here).
  * hProb: host result.  hPerm: nullable host Per(U_ST).
  * dWork: 256-byte-aligned workspace of prob_sample_workspace_size(n) bytes.
- * U_ST is gathered on the device and Per(U_ST) is the Glynn kernel's; the call
- * synchronises `stream` and returns with *hProb written. */
+ * U_ST is gathered on the device and Per(U_ST) is the Glynn kernel's; with
+ * repeated output (or input) modes the distinct columns (or rows, through the
+ * transpose) go through perm_glynn_mult, whichever orientation has fewer terms.
+ * The call synchronises `stream` and returns with *hProb written. */
 size_t prob_sample_workspace_size(int n, const perm_opts* opts);
 int prob_sample(const perm_c128* dU, int m, int ldu, const int32_t* hS, const int32_t* hT, double* hProb,
                 perm_c128* hPerm, void* dWork, size_t workBytes, const perm_opts* opts, void* stream);

@@ -10,6 +10,7 @@ Functions mirror the C entry points:
 * :func:`glynn`  -- Per(A), BB/FG formula (Supp. Eq. (S2), Algorithm 2 of arXiv 1606.05836)
 * :func:`ryser`  -- Per(A), Ryser formula (Supp. Eq. (S1), Algorithm 1)
 * :func:`ryser_nw` -- Per(A), Ryser's formula halved to 2^(n-1) subsets
+* :func:`glynn_mult` -- Per with repeated columns (photon collisions), multiplicity expansion
 * :func:`glynn_range`, :func:`ryser_range` -- partial sums over a Gray-index range
 * :func:`batched`, :class:`BatchedPermanents` -- many permanents of mixed sizes in
   one persistent launch (CUDA-graph capture, autotuned launch shape)
@@ -26,7 +27,7 @@ import torch
 from . import _native
 from ._native import PERM_MAX_N, PRECISIONS, Opts, PermError
 
-__all__ = ["glynn", "ryser", "ryser_nw", "glynn_range", "ryser_range", "workspace_size", "PermError", "PERM_MAX_N",
+__all__ = ["glynn", "glynn_mult", "ryser", "ryser_nw", "glynn_range", "ryser_range", "workspace_size", "PermError", "PERM_MAX_N",
            "PRECISIONS", "library", "batched", "BatchedPermanents", "grad", "PermAbs2", "prob"]
 
 _workspaces: dict = {}
@@ -132,6 +133,37 @@ def prob(U: torch.Tensor, s, t, prec="fp64", chunk_log2=0, block=0, grid=0):
                              nbytes, ctypes.byref(o), ctypes.c_void_p(_stream_ptr(dev)))
     _native.check(st, "prob_sample")
     return p.value, complex(per[0], per[1])
+
+
+def glynn_mult(B: torch.Tensor, mult, prec="fp64", chunk_log2=0, block=0, grid=0) -> torch.Tensor:
+    """Per of the n x n matrix whose columns are B[:, c] repeated mult[c] times
+    (B: n x g complex128 CUDA tensor, sum(mult) = n), by the multiplicity expansion
+    of the Glynn sum; returns a 0-dim complex128 CUDA tensor."""
+    import numpy as np
+
+    lib = library()
+    if not isinstance(B, torch.Tensor) or not B.is_cuda or B.dtype != torch.complex128 or B.dim() != 2:
+        raise TypeError("B must be a 2-D complex128 CUDA tensor")
+    B = B.contiguous()
+    n, g = B.shape
+    mult = np.ascontiguousarray(np.asarray(mult, dtype=np.int32))
+    if mult.shape != (g,):
+        raise ValueError("mult must have one entry per column of B")
+    o = _opts(prec=prec, chunk_log2=chunk_log2, block=block, grid=grid)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    dev = B.device
+    out = torch.empty(1, dtype=torch.complex128, device=dev)
+    with torch.cuda.device(dev):
+        nbytes = int(lib.perm_glynn_mult_workspace_size(n, g, mult.ctypes.data_as(i32p), ctypes.byref(o)))
+        if nbytes == 0:
+            raise ValueError("invalid multiplicities %s for n = %d" % (mult.tolist(), n))
+        ws = _workspace(dev, nbytes + 256)
+        base = (ws.data_ptr() + 255) & ~255
+        st = lib.perm_glynn_mult(ctypes.c_void_p(B.data_ptr()), n, g, g, mult.ctypes.data_as(i32p),
+                                 ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(base), nbytes, ctypes.byref(o),
+                                 ctypes.c_void_p(_stream_ptr(dev)))
+    _native.check(st, "perm_glynn_mult")
+    return out[0]
 
 
 def ryser_nw(A: torch.Tensor, prec="fp64", chunk_log2=0, block=0, grid=0) -> torch.Tensor:

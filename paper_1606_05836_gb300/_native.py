@@ -12,8 +12,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "lib", "libperm.so")
 
 PERM_MAX_N = 48
-PERM_FP64, PERM_FP64_DD, PERM_FP32P_DD = 0, 1, 2
-PRECISIONS = {"fp64": PERM_FP64, "fp64_dd": PERM_FP64_DD, "fp32p_dd": PERM_FP32P_DD}
+PERM_FP64, PERM_FP64_DD, PERM_FP32P_DD, PERM_FP64_DF = 0, 1, 2, 3
+PRECISIONS = {"fp64": PERM_FP64, "fp64_dd": PERM_FP64_DD, "fp32p_dd": PERM_FP32P_DD, "fp64_df": PERM_FP64_DF}
 
 # every symbol include/perm.h declares
 EXPORTS = (
@@ -25,6 +25,8 @@ EXPORTS = (
     "perm_ryser_range",
     "perm_batched_workspace_size",
     "perm_batched",
+    "perm_glynn_mult_workspace_size",
+    "perm_glynn_mult",
     "prob_sample_workspace_size",
     "prob_sample",
     "perm_grad_workspace_size",
@@ -78,6 +80,10 @@ def load(path: str | None = None):
     lib.perm_batched_workspace_size.restype = sz
     lib.perm_batched.argtypes = [vp, vp, vp, i32p, i32, i32, vp, vp, vp, vp, sz, op, vp]
     lib.perm_batched.restype = i32
+    lib.perm_glynn_mult_workspace_size.argtypes = [i32, i32, i32p, op]
+    lib.perm_glynn_mult_workspace_size.restype = sz
+    lib.perm_glynn_mult.argtypes = [vp, i32, i32, i32, i32p, vp, vp, sz, op, vp]
+    lib.perm_glynn_mult.restype = i32
     lib.prob_sample_workspace_size.argtypes = [i32, op]
     lib.prob_sample_workspace_size.restype = sz
     lib.prob_sample.argtypes = [vp, i32, i32, i32p, i32p, ctypes.POINTER(ctypes.c_double), vp, vp, sz, op, vp]

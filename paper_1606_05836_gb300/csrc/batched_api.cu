@@ -193,7 +193,7 @@ int batch_opts(const perm_opts* o, int* prec, int* chunk, int* unit, int* block,
   *unit = (o && o->unit_log2) ? o->unit_log2 : 11;
   *block = (o && o->block) ? o->block : 128;
   *grid = o ? o->grid : 0;
-  if (*prec < PERM_FP64 || *prec > PERM_FP32P_DD) return PERM_EINVAL;
+  if (*prec < PERM_FP64 || *prec > PERM_FP32P_DD) return PERM_EINVAL;  // the batched walk has rungs R0-R2
   if (*chunk < 1 || *chunk > 30 || *unit < 0 || *unit > 30) return PERM_EINVAL;
   if (*block < 32 || *block > 256 || (*block & 31) || *grid < 0) return PERM_EINVAL;
   return PERM_OK;

@@ -16,11 +16,45 @@ namespace permk {
 // KIND_RYSER_NW: Ryser's formula over the 2^(n-1) subsets of the first n-1
 // columns, Per = (-1)^(n-1) 2 sum_S (-1)^|S| prod_i (x_i + sum_{j in S} a_ij),
 // x_i = a_{i,n-1} - (1/2) sum_j a_ij (Nijenhuis and Wilf's halving of Eq. (S1)).
-// KIND_GLYNN_BASE: Eq. (S2) for a matrix with repeated columns, one term class of
-// the multiplicity expansion: v_i = x_i + sum_{j in F} delta_j a_ij over the
-// free (non-repeated) columns F, x = a fixed combination of the repeated
-// columns (base vector Xb), delta_j = -1 iff bit j of g(k) is set.
-enum { KIND_GLYNN = 0, KIND_RYSER = 1, KIND_RYSER_NW = 2, KIND_GLYNN_BASE = 3 };
+// KIND_GLYNN_MULT: Eq. (S2) for a matrix with repeated columns (see MultInfo):
+// one class of the multiplicity expansion at a time, v_i = sum_c coef_c b_ic
+// over the distinct columns b_c, coef = +-1 for the free (non-repeated)
+// columns (-1 iff their bit of g(k) is set), +1 for the fixed singleton, and
+// m_c - 2 k_c for a repeated group whose class digit is k_c.
+enum { KIND_GLYNN = 0, KIND_RYSER = 1, KIND_RYSER_NW = 2, KIND_GLYNN_MULT = 3 };
+
+// Column structure of a matrix with repeated columns.  Group c (distinct column
+// c) is free column role[c] >= 0, the fixed delta = +1 singleton (role -1), or a
+// repeated group (role -2) whose class digit k_c = (cls / radix_base[c]) %
+// radix[c] counts its -1 signs; radix = m + 1 (m for the group holding the
+// fixed copy) and the class weight is prod C(radix_c - 1, k_c) (-1)^k_c.
+struct MultInfo {
+  int g;
+  int nfree;
+  signed char role[48];
+  unsigned char mult[48];
+  unsigned char radix[48];
+  long long radix_base[48];
+};
+
+__device__ __forceinline__ int mult_digit(const MultInfo& mi, int c, long long cls) {
+  return (int)((cls / mi.radix_base[c]) % mi.radix[c]);
+}
+
+// prod_c C(radix_c - 1, k_c) (-1)^k_c over the repeated groups (exact: < 2^53)
+__device__ inline double mult_class_weight(const MultInfo& mi, long long cls) {
+  double w = 1.0;
+  int sign = 0;
+  for (int c = 0; c < mi.g; c++) {
+    if (mi.role[c] != -2) continue;
+    const int m = mi.radix[c] - 1, k = mult_digit(mi, c, cls);
+    double b = 1.0;
+    for (int i = 1; i <= k; i++) b = b * (double)(m - k + i) / (double)i;
+    w *= b;
+    sign ^= (k & 1);
+  }
+  return sign ? -w : w;
+}
 
 // ---------------------------------------------------------------------------
 // small helpers (integer-pipe sign handling, double-double)
@@ -166,6 +200,77 @@ __device__ __forceinline__ void prod_f32(const double (&vr)[N], const double (&v
 }
 
 // ---------------------------------------------------------------------------
+// R3: double-float products (pairs of FP32 on the FP32 pipe)
+// ---------------------------------------------------------------------------
+
+struct df {
+  float h, l;
+};
+
+// Exact split of an FP64 value into hi + lo FP32 halves on the integer pipe:
+// hi = the 53-bit mantissa rounded to 24 bits, lo = the rounded residual (24 of
+// its <= 29 bits), so hi + lo carries ~48 bits.  |x| < 2^-126 flushes hi to 0
+// and |x| < 2^-74 flushes lo to 0 (rows are pre-scaled to norm ~1).
+__device__ __forceinline__ df f64_to_df(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+  const int e = (int)((u >> 52) & 0x7FFull);
+  const long long m = (long long)((u & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+  const long long H = (m + (1ll << 28)) >> 29;
+  const long long R = m - (H << 29);
+  unsigned hb = ((unsigned)(e - 897) << 23) + (unsigned)H;
+  hb = (e > 896) ? hb : 0u;
+  hb = (e < 1151) ? hb : 0x7F800000u;
+  const int le = e - 948;  // biased FP32 exponent of 2^(e - 1075), the residual's unit
+  const float unit = __uint_as_float((le > 0 && le < 255) ? ((unsigned)le << 23) : 0u);
+  const float lo = __fmul_rn(__int2float_rn((int)R), unit);
+  return df{__uint_as_float(sign | hb), __uint_as_float(__float_as_uint(lo) ^ sign)};
+}
+
+// (xr + i xi) <- (xr + i xi)(yr + i yi) in double-float: exact products of the
+// high parts (two-product by FMA), a two-sum of the two, the cross terms with the
+// low parts folded in by FMA, then renormalisation.  The _rn intrinsics keep the
+// compiler from contracting the error-free transformations.
+__device__ __forceinline__ void dfc_mul(df& xr, df& xi, const df yr, const df yi) {
+  const float p1 = __fmul_rn(xr.h, yr.h), e1 = __fmaf_rn(xr.h, yr.h, -p1);
+  const float p2 = __fmul_rn(xi.h, yi.h), e2 = __fmaf_rn(xi.h, yi.h, -p2);
+  const float s = __fsub_rn(p1, p2);
+  const float bb = __fsub_rn(s, p1);
+  const float es = __fadd_rn(__fsub_rn(p1, __fsub_rn(s, bb)), __fsub_rn(-p2, bb));
+  float t = __fadd_rn(es, __fsub_rn(e1, e2));
+  t = __fmaf_rn(xr.h, yr.l, t);
+  t = __fmaf_rn(xr.l, yr.h, t);
+  t = __fmaf_rn(-xi.h, yi.l, t);
+  t = __fmaf_rn(-xi.l, yi.h, t);
+  const float rh = __fadd_rn(s, t);
+  const float rl = __fsub_rn(t, __fsub_rn(rh, s));
+  const float q1 = __fmul_rn(xr.h, yi.h), f1 = __fmaf_rn(xr.h, yi.h, -q1);
+  const float q2 = __fmul_rn(xi.h, yr.h), f2 = __fmaf_rn(xi.h, yr.h, -q2);
+  const float u = __fadd_rn(q1, q2);
+  const float cc = __fsub_rn(u, q1);
+  const float eu = __fadd_rn(__fsub_rn(q1, __fsub_rn(u, cc)), __fsub_rn(q2, cc));
+  float v = __fadd_rn(eu, __fadd_rn(f1, f2));
+  v = __fmaf_rn(xr.h, yi.l, v);
+  v = __fmaf_rn(xr.l, yi.h, v);
+  v = __fmaf_rn(xi.h, yr.l, v);
+  v = __fmaf_rn(xi.l, yr.h, v);
+  const float ih = __fadd_rn(u, v);
+  const float il = __fsub_rn(v, __fsub_rn(ih, u));
+  xr = df{rh, rl};
+  xi = df{ih, il};
+}
+
+// prod_i v_i in double-float, returned as FP64 (hi + lo is exact in FP64)
+template <int N>
+__device__ __forceinline__ void prod_df(const double (&vr)[N], const double (&vi)[N], double& pr, double& pi) {
+  df ar = f64_to_df(vr[0]), ai = f64_to_df(vi[0]);
+#pragma unroll
+  for (int i = 1; i < N; i++) dfc_mul(ar, ai, f64_to_df(vr[i]), f64_to_df(vi[i]));
+  pr = f32_to_f64_int(ar.h) + f32_to_f64_int(ar.l);
+  pi = f32_to_f64_int(ai.h) + f32_to_f64_int(ai.l);
+}
+
+// ---------------------------------------------------------------------------
 // one thread's Gray walk over [kb, ke) (steps a2-a5)
 // ---------------------------------------------------------------------------
 
@@ -182,18 +287,22 @@ __device__ __forceinline__ double2 ldcol(const double2* p) {
 // vector Xb), coef_b = [bit b] over the first n-1 columns); every other step
 // adds +-Step[b], b = ctz(k).  Columns are `stride` complex numbers apart.
 // GLOBAL selects read-only global loads instead of shared-memory loads.
+// KIND_GLYNN_MULT: Acol holds the g distinct columns, Step the doubled free
+// columns (by free index), mi the column structure and cls the class; [kb, ke)
+// are Gray indices of the free columns within that class.
 template <int N, int PREC, int TUNE, bool GLOBAL>
 __device__ __forceinline__ void walk_range(const double2* __restrict__ Acol, const double2* __restrict__ Step,
-                                           const double2* __restrict__ Xb, int stride, int kind, int base_cols,
-                                           uint64_t kb, uint64_t ke, uint64_t CH, double nz, double& ar, double& ai,
-                                           double& cr, double& ci) {
+                                           const double2* __restrict__ Xb, const MultInfo* mi, long long cls,
+                                           int stride, int kind, uint64_t kb, uint64_t ke, uint64_t CH, double nz,
+                                           double& ar, double& ai, double& cr, double& ci) {
   const bool glynn = (kind == KIND_GLYNN);
-  const bool glynn_signs = glynn || kind == KIND_GLYNN_BASE;
-  const bool has_base = (kind == KIND_RYSER_NW || kind == KIND_GLYNN_BASE);
+  const bool multk = (kind == KIND_GLYNN_MULT);
+  const bool glynn_signs = glynn || multk;
+  const bool has_base = (kind == KIND_RYSER_NW);
   // Glynn: a set Gray bit means delta = -1 (subtract 2a when it turns on);
   // Ryser: a set bit means the column is in S (add a when it turns on).
   const unsigned long long on_mask = glynn_signs ? 0x8000000000000000ull : 0ull;
-  const int ncols = (kind == KIND_RYSER_NW) ? N - 1 : (kind == KIND_GLYNN_BASE ? base_cols : N);
+  const int ncols = (kind == KIND_RYSER_NW) ? N - 1 : (multk ? mi->g : N);
   for (uint64_t c0 = kb; c0 < ke; c0 += CH) {
     const uint64_t c1 = (ke - c0 > CH) ? c0 + CH : ke;
     uint64_t g = c0 ^ (c0 >> 1);
@@ -213,9 +322,16 @@ __device__ __forceinline__ void walk_range(const double2* __restrict__ Acol, con
 #pragma unroll 1
     for (int j = 0; j < ncols; j++) {
       double coef;
-      if (glynn) coef = (j == 0) ? 1.0 : (((g >> (j - 1)) & 1ull) ? -1.0 : 1.0);
-      else if (kind == KIND_GLYNN_BASE) coef = ((g >> j) & 1ull) ? -1.0 : 1.0;
-      else coef = ((g >> j) & 1ull) ? 1.0 : 0.0;
+      if (glynn) {
+        coef = (j == 0) ? 1.0 : (((g >> (j - 1)) & 1ull) ? -1.0 : 1.0);
+      } else if (multk) {
+        const int role = mi->role[j];
+        if (role >= 0) coef = ((g >> role) & 1ull) ? -1.0 : 1.0;
+        else if (role == -1) coef = 1.0;
+        else coef = (double)(mi->mult[j] - 2 * mult_digit(*mi, j, cls));
+      } else {
+        coef = ((g >> j) & 1ull) ? 1.0 : 0.0;
+      }
       const double2* col = Acol + j * stride;
 #pragma unroll
       for (int i = 0; i < N; i++) {
@@ -231,6 +347,11 @@ __device__ __forceinline__ void walk_range(const double2* __restrict__ Acol, con
       const unsigned long long smask = (k & 1ull) << 63;
       if (PREC == 0) {
         term_r0<N, TUNE>(vr, vi, smask, ar, ai, nz);
+      } else if (PREC == 3) {
+        double pr, pi;
+        prod_df<N>(vr, vi, pr, pi);
+        ar += xor_sign(pr, smask);
+        ai += xor_sign(pi, smask);
       } else {
         double pr, pi;
         if (PREC == 1) prod_f64<N, TUNE>(vr, vi, pr, pi, nz);
@@ -281,7 +402,7 @@ __device__ __forceinline__ void warp_sum_dd(dd& sr, dd& si) {
 // Per-thread (sum, compensation) -> normalised double-double.
 template <int PREC>
 __device__ __forceinline__ void acc_to_dd(double ar, double ai, double cr, double ci, dd& sr, dd& si) {
-  if (PREC != 0) {
+  if (PREC == 1 || PREC == 2) {
     sr = dd_add(dd{ar, 0.0}, dd{cr, 0.0});
     si = dd_add(dd{ai, 0.0}, dd{ci, 0.0});
   } else {

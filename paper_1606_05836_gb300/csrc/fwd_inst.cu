@@ -19,7 +19,7 @@ static int launch_one(const FwdArgs& a, int grid, int block, cudaStream_t s) {
   const size_t smem = fwd_smem_bytes(N, a.kind);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(fwd_kernel<N, PREC, TUNE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)fwd_smem_bytes(N, KIND_GLYNN_BASE));
+                                         (int)fwd_smem_bytes(N, KIND_GLYNN));
     if (e != cudaSuccess) return (int)e;
   }
   fwd_kernel<N, PREC, TUNE><<<grid, block, smem, s>>>(a);
@@ -31,7 +31,7 @@ static int occupancy_one(int block, int kind, int* out) {
   const size_t smem = fwd_smem_bytes(N, kind);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(fwd_kernel<N, PREC, TUNE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)fwd_smem_bytes(N, KIND_GLYNN_BASE));
+                                         (int)fwd_smem_bytes(N, KIND_GLYNN));
     if (e != cudaSuccess) return (int)e;
   }
   return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, fwd_kernel<N, PREC, TUNE>, block, smem);
@@ -47,6 +47,7 @@ template <int N>
 int launch_fwd(const FwdArgs& a, int prec, int tune, int grid, int block, cudaStream_t s) {
   if (prec == 1) return launch_one<N, 1, PERM_DEFAULT_TUNE>(a, grid, block, s);
   if (prec == 2) return launch_one<N, 2, PERM_DEFAULT_TUNE>(a, grid, block, s);
+  if (prec == 3) return launch_one<N, 3, PERM_DEFAULT_TUNE>(a, grid, block, s);
   if constexpr (HasTuneVariants<N>::value) {
     switch (tune) {
       case 0: return launch_one<N, 0, 0>(a, grid, block, s);
@@ -63,6 +64,7 @@ template <int N>
 int fwd_blocks_per_sm(int prec, int tune, int block, int kind, int* out) {
   if (prec == 1) return occupancy_one<N, 1, PERM_DEFAULT_TUNE>(block, kind, out);
   if (prec == 2) return occupancy_one<N, 2, PERM_DEFAULT_TUNE>(block, kind, out);
+  if (prec == 3) return occupancy_one<N, 3, PERM_DEFAULT_TUNE>(block, kind, out);
   if constexpr (HasTuneVariants<N>::value) {
     switch (tune) {
       case 0: return occupancy_one<N, 0, 0>(block, kind, out);

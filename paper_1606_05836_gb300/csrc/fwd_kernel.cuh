@@ -30,15 +30,9 @@ struct FwdArgs {
   unsigned* ticket; // zero before launch; reset to zero by the last block
   double2* out;     // raw == 0: one value, the permanent; raw == 1: (hi, lo) partial sum
   int raw;
-  // KIND_GLYNN_BASE only: A holds the g distinct columns (n x g, lda); column c is
-  // free column role[c] >= 0, part of the base vector with coefficient coef[c]
-  // (role -2), or the fixed delta = +1 singleton (role -1).  The raw partial sum
-  // is multiplied by `weight`.
-  int g;
-  int nfree;
-  double weight;
-  signed char role[48];
-  short coef[48];
+  // KIND_GLYNN_MULT only: A holds the g distinct columns (n x g, lda); the Gray
+  // range runs over (class, free index) pairs, K = class * 2^nfree + free index.
+  MultInfo mult;
 };
 
 // ---------------------------------------------------------------------------
@@ -106,13 +100,12 @@ __device__ int stage_matrix(const double2* __restrict__ A, int lda, int kind, do
   return total;
 }
 
-// Staging for KIND_GLYNN_BASE: rows scaled by 2^{s_i} from the norms of the g
-// distinct columns; free columns to Acol / Step (doubled); the base vector
-// x_i = sum_{role -2} coef_c b_ic + sum_{role -1} b_ic to Xb.
+// Staging for KIND_GLYNN_MULT: rows scaled by 2^{s_i} from the norms of the g
+// distinct columns; all distinct columns to Acol, the free ones doubled to Step.
 template <int N>
-__device__ int stage_matrix_base(const FwdArgs& a, double2* Acol, double2* Step, double2* Xb, int* s_row) {
+__device__ int stage_matrix_mult(const FwdArgs& a, double2* Acol, double2* Step, int* s_row) {
   constexpr int NP = Stride<N>::value;
-  const int g = a.g;
+  const int g = a.mult.g;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     double nrm = 0.0;
     for (int c = 0; c < g; c++) {
@@ -125,21 +118,13 @@ __device__ int stage_matrix_base(const FwdArgs& a, double2* Acol, double2* Step,
     s = s > 1000 ? 1000 : (s < -1000 ? -1000 : s);
     s_row[i] = s;
     const double f = pow2_double(s);
-    double xr = 0.0, xi = 0.0;
     for (int c = 0; c < g; c++) {
       const double2 v = a.A[(size_t)i * a.lda + c];
       const double br = v.x * f, bi = v.y * f;
-      const int role = a.role[c];
-      if (role >= 0) {
-        Acol[role * NP + i] = make_double2(br, bi);
-        Step[role * NP + i] = make_double2(br + br, bi + bi);
-      } else {
-        const double k = (role == -1) ? 1.0 : (double)a.coef[c];
-        xr = fma(k, br, xr);
-        xi = fma(k, bi, xi);
-      }
+      Acol[c * NP + i] = make_double2(br, bi);
+      const int role = a.mult.role[c];
+      if (role >= 0) Step[role * NP + i] = make_double2(br + br, bi + bi);
     }
-    Xb[i] = make_double2(xr, xi);
   }
   __syncthreads();
   int total = 0;
@@ -157,13 +142,11 @@ __global__ void __launch_bounds__(256, 1) fwd_kernel(FwdArgs a) {
   extern __shared__ double2 smem[];
   double2* Acol = smem;
   constexpr int NP = Stride<N>::value;
-  double2* Step = (a.kind == KIND_GLYNN || a.kind == KIND_GLYNN_BASE) ? smem + N * NP : smem;
-  // base vector: Ryser-NW keeps it in the (unused) second half, the
-  // multiplicity kind after the step columns
-  double2* Xb = (a.kind == KIND_GLYNN_BASE) ? smem + 2 * N * NP : smem + N * NP;
+  double2* Step = (a.kind == KIND_GLYNN || a.kind == KIND_GLYNN_MULT) ? smem + N * NP : smem;
+  double2* Xb = smem + N * NP;  // Ryser-NW base vector (the otherwise unused second half)
   __shared__ int s_row[N];
 
-  const int scale_exp = (a.kind == KIND_GLYNN_BASE) ? stage_matrix_base<N>(a, Acol, Step, Xb, s_row)
+  const int scale_exp = (a.kind == KIND_GLYNN_MULT) ? stage_matrix_mult<N>(a, Acol, Step, s_row)
                                                     : stage_matrix<N>(a.A, a.lda, a.kind, Acol, Step, s_row, Xb);
   const double nz = a.neg_zero;
 
@@ -175,11 +158,34 @@ __global__ void __launch_bounds__(256, 1) fwd_kernel(FwdArgs a) {
 
   double ar = 0.0, ai = 0.0, cr = 0.0, ci = 0.0;  // accumulator and (R1/R2) compensation
 
-  walk_range<N, PREC, TUNE, false>(Acol, Step, Xb, NP, a.kind, a.nfree, kb, ke, CH, nz, ar, ai, cr, ci);
+  dd sr, si;
+  if (a.kind == KIND_GLYNN_MULT) {
+    // split the range at class boundaries; each class's sum times its weight
+    const int f = a.mult.nfree;
+    sr = dd{0.0, 0.0};
+    si = dd{0.0, 0.0};
+    uint64_t K = kb;
+    while (K < ke) {
+      const long long cls = (long long)(K >> f);
+      const uint64_t next = ((uint64_t)cls + 1) << f;
+      const uint64_t seg_end = next < ke ? next : ke;
+      const uint64_t lb = K & ((1ull << f) - 1);
+      double gr = 0.0, gi = 0.0, hr = 0.0, hi = 0.0;
+      walk_range<N, PREC, TUNE, false>(Acol, Step, nullptr, &a.mult, cls, NP, a.kind, lb, lb + (seg_end - K), CH, nz,
+                                       gr, gi, hr, hi);
+      dd pr, pi;
+      acc_to_dd<PREC>(gr, gi, hr, hi, pr, pi);
+      const double w = mult_class_weight(a.mult, cls);
+      sr = dd_add(sr, dd{pr.hi * w, pr.lo * w});
+      si = dd_add(si, dd{pi.hi * w, pi.lo * w});
+      K = seg_end;
+    }
+  } else {
+    walk_range<N, PREC, TUNE, false>(Acol, Step, Xb, nullptr, 0, NP, a.kind, kb, ke, CH, nz, ar, ai, cr, ci);
+    acc_to_dd<PREC>(ar, ai, cr, ci, sr, si);
+  }
 
   // ---- reduction (step a6): warp butterfly, block, last-block grid sum ------
-  dd sr, si;
-  acc_to_dd<PREC>(ar, ai, cr, ci, sr, si);
   warp_sum_dd(sr, si);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
@@ -226,7 +232,7 @@ __global__ void __launch_bounds__(256, 1) fwd_kernel(FwdArgs a) {
       // undo the row scaling; Glynn divides by 2^(n-1); Ryser multiplies by (-1)^n
       // Ryser-NW: x 2 (-1)^(n-1)
       int e = -scale_exp;
-      if (!a.raw && glynn) e -= (N - 1);
+      if (!a.raw && (glynn || a.kind == KIND_GLYNN_MULT)) e -= (N - 1);
       if (!a.raw && a.kind == KIND_RYSER_NW) e += 1;
       double neg = 1.0;
       if (!a.raw && a.kind == KIND_RYSER && (N & 1)) neg = -1.0;
@@ -236,9 +242,8 @@ __global__ void __launch_bounds__(256, 1) fwd_kernel(FwdArgs a) {
       ti.hi = ldexp(ti.hi, e) * neg;
       ti.lo = ldexp(ti.lo, e) * neg;
       if (a.raw) {
-        const double w = (a.kind == KIND_GLYNN_BASE) ? a.weight : 1.0;
-        a.out[0] = make_double2(tr.hi * w, ti.hi * w);
-        a.out[1] = make_double2(tr.lo * w, ti.lo * w);
+        a.out[0] = make_double2(tr.hi, ti.hi);
+        a.out[1] = make_double2(tr.lo, ti.lo);
       } else {
         a.out[0] = make_double2(tr.hi + tr.lo, ti.hi + ti.lo);
       }
@@ -254,7 +259,7 @@ template <int N>
 int fwd_blocks_per_sm(int prec, int tune, int block, int kind, int* out);
 
 inline size_t fwd_smem_bytes(int N, int kind) {
-  const size_t cols = (kind == KIND_RYSER) ? (size_t)N : (kind == KIND_GLYNN_BASE ? 2 * (size_t)N + 1 : 2 * (size_t)N);
+  const size_t cols = (kind == KIND_RYSER) ? (size_t)N : 2 * (size_t)N;
   return cols * (N | 1) * sizeof(double2);
 }
 

@@ -10,6 +10,8 @@
 #include "host_util.h"
 #include "perm.h"
 
+using permk::dd;
+
 namespace {
 
 thread_local int g_last_cuda = 0;
@@ -89,7 +91,7 @@ int read_opts(const perm_opts* o, int* prec, int* chunk_log2, int* block, int* g
   *chunk_log2 = (o && o->chunk_log2) ? o->chunk_log2 : 12;
   *block = (o && o->block) ? o->block : 128;
   *grid = o ? o->grid : 0;
-  if (*prec < PERM_FP64 || *prec > PERM_FP32P_DD) return PERM_EINVAL;
+  if (*prec < PERM_FP64 || *prec > PERM_FP64_DF) return PERM_EINVAL;
   if (*chunk_log2 < 1 || *chunk_log2 > 30) return PERM_EINVAL;
   if (*block < 32 || *block > 256 || (*block & 31)) return PERM_EINVAL;
   if (*grid < 0) return PERM_EINVAL;
@@ -181,17 +183,18 @@ int run_fwd(const perm_c128* dA, int n, int lda, int kind, uint64_t k_begin, uin
 struct GatherArgs {
   const double2* U;
   int ldu;
-  int n;
+  int n;           // rows of the gathered matrix
+  int ncols;       // its columns
+  int transpose;   // 0: out[r][c] = U[rows[r]][cols[c]];  1: out[r][c] = U[cols[c]][rows[r]]
   int rows[PERM_MAX_N];
   int cols[PERM_MAX_N];
-  double2* out;  // n x n, row-major
+  double2* out;    // n x ncols, row-major
 };
 
-// U_ST[r][c] = U[rows[r]][cols[c]]
 __global__ void gather_ust_kernel(GatherArgs g) {
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.n * g.n; idx += gridDim.x * blockDim.x) {
-    const int r = idx / g.n, c = idx % g.n;
-    g.out[idx] = g.U[(size_t)g.rows[r] * g.ldu + g.cols[c]];
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.n * g.ncols; idx += gridDim.x * blockDim.x) {
+    const int r = idx / g.ncols, c = idx % g.ncols;
+    g.out[idx] = g.transpose ? g.U[(size_t)g.cols[c] * g.ldu + g.rows[r]] : g.U[(size_t)g.rows[r] * g.ldu + g.cols[c]];
   }
 }
 
@@ -201,9 +204,113 @@ __global__ void prob_epilogue_kernel(const double2* per, double scale, double* p
   prob[0] = fma(p.x, p.x, p.y * p.y) * scale;
 }
 
-size_t prob_ws_offset_ust() { return 0; }
 size_t prob_ws_offset_res(int n) { return ((size_t)n * n * sizeof(double2) + 255) & ~(size_t)255; }
-size_t prob_ws_offset_fwd(int n) { return prob_ws_offset_res(n) + 256; }
+size_t prob_ws_offset_sub(int n) { return prob_ws_offset_res(n) + 256; }
+
+// --- repeated columns (multiplicity expansion of Eq. (S2)) ---------------------
+
+struct MultPlan {
+  int n, g, nfree;
+  int fixed;             // group whose first copy has delta = +1
+  int role[PERM_MAX_N];  // per group: free column index, -1 fixed singleton, -2 repeated
+  int mult[PERM_MAX_N];
+  int radix[PERM_MAX_N];
+  long long radix_base[PERM_MAX_N];
+  long long classes;     // number of classes (combinations of the repeated groups)
+  double terms;          // classes x 2^nfree
+};
+
+// Groups: c = 0..g-1 with multiplicities m_c (sum n).  A group of m >= 2 copies
+// enters through k = the number of its -1 signs (radix m + 1, weight C(m, k));
+// singletons are free binary columns.  The delta = +1 copy is taken from a
+// singleton if there is one (halving the free range), otherwise from the smallest
+// repeated group (its k then runs over 0..m-1 with weight C(m-1, k)).
+int mult_plan(int n, int g, const int32_t* mult, MultPlan* P) {
+  if (g < 1 || g > n || n > PERM_MAX_N) return PERM_ERANGE;
+  int sum = 0;
+  for (int c = 0; c < g; c++) {
+    if (mult[c] < 1) return PERM_EINVAL;
+    sum += mult[c];
+    P->mult[c] = mult[c];
+  }
+  if (sum != n) return PERM_EINVAL;
+  P->n = n;
+  P->g = g;
+  int fixed = -1;
+  for (int c = 0; c < g; c++)
+    if (mult[c] == 1) {
+      fixed = c;
+      break;
+    }
+  if (fixed < 0) {
+    fixed = 0;
+    for (int c = 1; c < g; c++)
+      if (mult[c] < mult[fixed]) fixed = c;
+  }
+  P->fixed = fixed;
+  int nfree = 0;
+  long long classes = 1;
+  for (int c = 0; c < g; c++) {
+    P->radix[c] = 0;
+    P->radix_base[c] = 1;
+    if (mult[c] == 1) {
+      P->role[c] = (c == fixed) ? -1 : nfree++;
+    } else {
+      P->role[c] = -2;
+      P->radix[c] = (c == fixed) ? mult[c] : mult[c] + 1;
+      P->radix_base[c] = classes;
+      classes *= P->radix[c];  // <= 2^(n-1) <= 2^47: a group of m copies has m + 1 <= 2^m classes
+    }
+  }
+  P->nfree = nfree;
+  P->classes = classes;
+  P->terms = (double)classes * (double)(1ull << nfree);
+  return PERM_OK;
+}
+
+int run_mult(const perm_c128* dB, int n, int ldb, int g, const int32_t* hMult, perm_c128* dOut, void* dWork,
+             size_t workBytes, const perm_opts* opts, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!dB || !dOut || !hMult || !dWork) return PERM_EINVAL;
+  if (((uintptr_t)dB & 15u) || ((uintptr_t)dOut & 15u) || ((uintptr_t)dWork & 15u)) return PERM_EINVAL;
+  if (ldb < g) return PERM_EINVAL;
+  MultPlan P;
+  int st = mult_plan(n, g, hMult, &P);
+  if (st) return st;
+  const uint64_t total = (uint64_t)P.classes << P.nfree;
+  Plan pl;
+  st = plan_fwd(n, permk::KIND_GLYNN_MULT, total, opts, &pl);
+  if (st) return st;
+  if (workBytes < workspace_for_grid(pl.grid)) return PERM_ENOMEM;
+  permk::FwdArgs a;
+  a.A = (const double2*)dB;
+  a.n = n;
+  a.lda = ldb;
+  a.kind = permk::KIND_GLYNN_MULT;
+  a.chunk_log2 = pl.chunk_log2;
+  a.k_begin = 0;
+  a.k_end = total;
+  a.per_q = pl.per_q;
+  a.per_r = pl.per_r;
+  a.neg_zero = -0.0;
+  a.ticket = (unsigned*)dWork;
+  a.partials = (double*)((char*)dWork + 256);
+  a.out = (double2*)dOut;
+  a.raw = 0;
+  a.mult.g = g;
+  a.mult.nfree = P.nfree;
+  for (int c = 0; c < g; c++) {
+    a.mult.role[c] = (signed char)P.role[c];
+    a.mult.mult[c] = (unsigned char)P.mult[c];
+    a.mult.radix[c] = (unsigned char)P.radix[c];
+    a.mult.radix_base[c] = P.radix_base[c];
+  }
+  cudaError_t e = cudaMemsetAsync(dWork, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return fail_cuda(e);
+  int le = dispatch_launch(n, a, pl.prec, pl.tune, pl.grid, pl.block, s);
+  if (le) return fail_cuda_int(le);
+  return PERM_OK;
+}
 
 }  // namespace
 
@@ -253,11 +360,25 @@ int perm_ryser_range(const perm_c128* dA, int n, int lda, uint64_t k_begin, uint
 }
 
 
+
+size_t perm_glynn_mult_workspace_size(int n, int g, const int32_t* hMult, const perm_opts* opts) {
+  if (!hMult || n < 1) return 0;
+  MultPlan P;
+  if (mult_plan(n, g, hMult, &P)) return 0;
+  return perm_workspace_size(n, opts);
+}
+
+int perm_glynn_mult(const perm_c128* dB, int n, int ldb, int g, const int32_t* hMult, perm_c128* dOut, void* dWork,
+                    size_t workBytes, const perm_opts* opts, void* stream) {
+  if (n < 1 || n > PERM_MAX_N) return PERM_ERANGE;
+  return run_mult(dB, n, ldb, g, hMult, dOut, dWork, workBytes, opts, stream);
+}
+
 size_t prob_sample_workspace_size(int n, const perm_opts* opts) {
   if (n < 0 || n > PERM_MAX_N) return 0;
   const size_t fwd = n >= 1 ? perm_workspace_size(n, opts) : 256;
   if (fwd == 0) return 0;
-  return prob_ws_offset_fwd(n) + fwd;
+  return prob_ws_offset_sub(n) + fwd;  // gathered matrix + result + kernel workspace
 }
 
 int prob_sample(const perm_c128* dU, int m, int ldu, const int32_t* hS, const int32_t* hT, double* hProb,
@@ -265,39 +386,93 @@ int prob_sample(const perm_c128* dU, int m, int ldu, const int32_t* hS, const in
   cudaStream_t s = (cudaStream_t)stream;
   if (m < 1 || !dU || ldu < m || !hS || !hT || !hProb || !dWork) return PERM_EINVAL;
   if (((uintptr_t)dU & 15u) || ((uintptr_t)dWork & 255u)) return PERM_EINVAL;
-  GatherArgs g;
-  int n = 0, nt = 0;
+  int rows[PERM_MAX_N], cols[PERM_MAX_N];           // input / output mode of every row / column of U_ST
+  int ins[PERM_MAX_N], s_mult[PERM_MAX_N], outs[PERM_MAX_N], t_mult[PERM_MAX_N];
+  int n = 0, nt = 0, gi = 0, go = 0;
+  bool rep_s = false, rep_t = false;
   double denom = 1.0;
   for (int i = 0; i < m; i++) {
     if (hS[i] < 0 || hT[i] < 0) return PERM_EINVAL;
+    if (hS[i] > PERM_MAX_N || hT[i] > PERM_MAX_N) return PERM_ERANGE;
     for (int k = 2; k <= hS[i]; k++) denom *= (double)k;
     for (int k = 2; k <= hT[i]; k++) denom *= (double)k;
+    if (hS[i] > 0) {
+      if (gi >= PERM_MAX_N) return PERM_ERANGE;
+      ins[gi] = i;
+      s_mult[gi++] = hS[i];
+      rep_s = rep_s || hS[i] > 1;
+    }
+    if (hT[i] > 0) {
+      if (go >= PERM_MAX_N) return PERM_ERANGE;
+      outs[go] = i;
+      t_mult[go++] = hT[i];
+      rep_t = rep_t || hT[i] > 1;
+    }
     for (int k = 0; k < hS[i]; k++) {
       if (n >= PERM_MAX_N) return PERM_ERANGE;
-      g.rows[n++] = i;
+      rows[n++] = i;
     }
     for (int k = 0; k < hT[i]; k++) {
       if (nt >= PERM_MAX_N) return PERM_ERANGE;
-      g.cols[nt++] = i;
+      cols[nt++] = i;
     }
   }
   if (n != nt) return PERM_EINVAL;
   if (workBytes < prob_sample_workspace_size(n, opts)) return PERM_ENOMEM;
   char* w = (char*)dWork;
-  double2* ust = (double2*)(w + prob_ws_offset_ust());
+  double2* mat = (double2*)w;
   double2* res = (double2*)(w + prob_ws_offset_res(n));
   double* prob = (double*)(w + prob_ws_offset_res(n) + 64);
+  char* sub = w + prob_ws_offset_sub(n);
+  const size_t sub_bytes = workBytes - prob_ws_offset_sub(n);
+  GatherArgs g;
   g.U = (const double2*)dU;
   g.ldu = ldu;
   g.n = n;
-  g.out = ust;
+  g.out = mat;
+  int st = PERM_OK;
+  // Photon collisions: repeated columns of U_ST (an output mode with t_j > 1) or
+  // repeated rows (s_i > 1, handled as columns of the transpose) go through the
+  // multiplicity expansion; the orientation with fewer terms is used.
+  int orient = 0;  // 0: plain; 1: columns = distinct outputs; 2: columns = distinct inputs
+  if (n > 0 && (rep_s || rep_t)) {
+    MultPlan pc, pr;
+    const bool ok_c = mult_plan(n, go, t_mult, &pc) == PERM_OK;
+    const bool ok_r = mult_plan(n, gi, s_mult, &pr) == PERM_OK;
+    if (ok_c && (!ok_r || pc.terms <= pr.terms)) orient = 1;
+    else if (ok_r) orient = 2;
+  }
+  if (orient == 1) {
+    for (int r = 0; r < n; r++) g.rows[r] = rows[r];
+    for (int c = 0; c < go; c++) g.cols[c] = outs[c];
+    g.ncols = go;
+    g.transpose = 0;
+  } else if (orient == 2) {
+    for (int r = 0; r < n; r++) g.rows[r] = cols[r];
+    for (int c = 0; c < gi; c++) g.cols[c] = ins[c];
+    g.ncols = gi;
+    g.transpose = 1;
+  } else {
+    for (int r = 0; r < n; r++) {
+      g.rows[r] = rows[r];
+      g.cols[r] = cols[r];
+    }
+    g.ncols = n;
+    g.transpose = 0;
+  }
   if (n > 0) {
-    gather_ust_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(g);
+    gather_ust_kernel<<<(n * g.ncols + 255) / 256, 256, 0, s>>>(g);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail_cuda(e);
   }
-  int st = run_fwd((const perm_c128*)ust, n, n, permk::KIND_GLYNN, 0, n >= 1 ? (1ull << (n - 1)) : 0, 0,
-                   (perm_c128*)res, w + prob_ws_offset_fwd(n), workBytes - prob_ws_offset_fwd(n), opts, stream);
+  if (orient == 1) {
+    st = run_mult((const perm_c128*)mat, n, go, go, t_mult, (perm_c128*)res, sub, sub_bytes, opts, stream);
+  } else if (orient == 2) {
+    st = run_mult((const perm_c128*)mat, n, gi, gi, s_mult, (perm_c128*)res, sub, sub_bytes, opts, stream);
+  } else {
+    st = run_fwd((const perm_c128*)mat, n, n, permk::KIND_GLYNN, 0, n >= 1 ? (1ull << (n - 1)) : 0, 0,
+                 (perm_c128*)res, sub, sub_bytes, opts, stream);
+  }
   if (st) return st;
   prob_epilogue_kernel<<<1, 1, 0, s>>>(res, 1.0 / denom, prob);
   cudaError_t e = cudaGetLastError();
