@@ -294,7 +294,7 @@ def measure_forms(dev, plain_rate):
     A20h = S.gaussian(20, 0)
     A20 = torch.as_tensor(A20h).to(dev)
     want20 = oracle.glynn(A20h)
-    for prec in ("fp64", "fp64_dd", "fp32p_dd"):
+    for prec in ("fp64", "fp64_dd", "fp32p_dd", "fp64_df"):
         pg.glynn(A32, prec=prec)
         t = timed(lambda: pg.glynn(A32, prec=prec))
         err = want20.rel_err(complex(pg.glynn(A20, prec=prec).cpu().item()))

@@ -55,7 +55,8 @@ def test_gaussian_small_all_rungs(pg, n):
     # 2^n-term cancellation amplifies it more than Glynn's.
     r2_tol = {"glynn": 1e-4, "ryser": 1e-2}
     for f in (pg.glynn, pg.ryser):
-        for prec, tol in (("fp64", REL_TOL), ("fp64_dd", REL_TOL), ("fp32p_dd", r2_tol[f.__name__])):
+        for prec, tol in (("fp64", REL_TOL), ("fp64_dd", REL_TOL), ("fp32p_dd", r2_tol[f.__name__]),
+                          ("fp64_df", REL_TOL)):
             got = val(f(dA, prec=prec))
             assert rel(got, want) < tol, (f.__name__, prec, got, want.hi)
 

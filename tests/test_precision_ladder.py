@@ -41,7 +41,7 @@ def ladder_errors(pg):
         dA = to_dev(A)
         errs = {}
         for method, f in (("glynn", pg.glynn), ("ryser", pg.ryser), ("ryser_nw", pg.ryser_nw)):
-            for prec in ("fp64", "fp64_dd", "fp32p_dd"):
+            for prec in ("fp64", "fp64_dd", "fp32p_dd", "fp64_df"):
                 got = val(f(dA, prec=prec))
                 errs[(method, prec)] = abs((got - want_hi) - want_lo) / abs(want_hi)
         out.append((row["kind"], n, errs))
@@ -51,12 +51,12 @@ def ladder_errors(pg):
 def test_precision_ladder(pg):
     results = ladder_errors(pg)
     print()
-    print("%-11s %3s  %-9s %-9s %-9s | %-9s %-9s %-9s | %-9s %-9s" % (
-        "input", "n", "G fp64", "G dd", "G fp32p", "R fp64", "R dd", "R fp32p", "NW fp64", "NW dd"))
+    print("%-11s %3s  %-9s %-9s %-9s %-9s | %-9s %-9s %-9s | %-9s %-9s" % (
+        "input", "n", "G fp64", "G dd", "G fp32p", "G df", "R fp64", "R dd", "R fp32p", "NW fp64", "NW dd"))
     for kind, n, e in results:
-        print("%-11s %3d  %.2e  %.2e  %.2e  | %.2e  %.2e  %.2e  | %.2e  %.2e" % (
+        print("%-11s %3d  %.2e  %.2e  %.2e  %.2e  | %.2e  %.2e  %.2e  | %.2e  %.2e" % (
             kind, n, e[("glynn", "fp64")], e[("glynn", "fp64_dd")], e[("glynn", "fp32p_dd")],
-            e[("ryser", "fp64")], e[("ryser", "fp64_dd")], e[("ryser", "fp32p_dd")],
+            e[("glynn", "fp64_df")], e[("ryser", "fp64")], e[("ryser", "fp64_dd")], e[("ryser", "fp32p_dd")],
             e[("ryser_nw", "fp64")], e[("ryser_nw", "fp64_dd")]))
     for kind, n, e in results:
         # FP64 Glynn meets the 1e-10 bar on every input, with or without compensation
@@ -66,6 +66,8 @@ def test_precision_ladder(pg):
         assert e[("glynn", "fp64_dd")] <= 4 * e[("glynn", "fp64")] + 1e-15, (kind, n)
         # the FP32-product rung has its own, stated error
         assert e[("glynn", "fp32p_dd")] < 1e-3, (kind, n)
+        # double-float products keep ~48 bits: still inside the FP64 bar
+        assert e[("glynn", "fp64_df")] < REL_TOL, (kind, n)
     # the paper's finding: on cancellation-heavy input Ryser in FP64 loses many
     # more digits than BB/FG (its "special-derived" matrices; all-ones errors
     # 10^7-10^9 apart)
