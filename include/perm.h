@@ -65,7 +65,7 @@ typedef enum {
   PERM_FP32P_DD = 2, /* R2: FP32 n-way products of the FP64 row sums, double-double accumulation */
   PERM_FP64_DF = 3   /* R3: the FP64 row sums split exactly into FP32 pairs and multiplied in
                         double-float arithmetic on the FP32 pipe (~48-bit products), FP64
-                        accumulation; single-permanent entry points only */
+                        accumulation */
 } perm_prec;
 
 /* Launch options; pass NULL for the defaults (every field 0 = default). */

@@ -29,7 +29,7 @@ NVFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I",
 # template instances build in parallel).
 MULTI = {
     "fwd_inst.cu": ["-DPERM_PART=%d" % p for p in range(8)],
-    "batched_inst.cu": ["-DPERM_PREC=%d" % p for p in range(3)],
+    "batched_inst.cu": ["-DPERM_PREC=%d" % p for p in range(4)],
     "grad_inst.cu": ["-DPERM_PART=%d" % p for p in range(4)],
 }
 

@@ -193,7 +193,7 @@ int batch_opts(const perm_opts* o, int* prec, int* chunk, int* unit, int* block,
   *unit = (o && o->unit_log2) ? o->unit_log2 : 11;
   *block = (o && o->block) ? o->block : 128;
   *grid = o ? o->grid : 0;
-  if (*prec < PERM_FP64 || *prec > PERM_FP32P_DD) return PERM_EINVAL;  // the batched walk has rungs R0-R2
+  if (*prec < PERM_FP64 || *prec > PERM_FP64_DF) return PERM_EINVAL;
   if (*chunk < 1 || *chunk > 30 || *unit < 0 || *unit > 30) return PERM_EINVAL;
   if (*block < 32 || *block > 256 || (*block & 31) || *grid < 0) return PERM_EINVAL;
   return PERM_OK;
@@ -228,12 +228,14 @@ int make_layout(int count, const int32_t* hN, int kind, int unit_log2, Layout* L
 int walk_launch(int prec, const BatchArgs& a, int grid, int block, cudaStream_t s) {
   if (prec == 1) return launch_batch_walk<1>(a, grid, block, s);
   if (prec == 2) return launch_batch_walk<2>(a, grid, block, s);
+  if (prec == 3) return launch_batch_walk<3>(a, grid, block, s);
   return launch_batch_walk<0>(a, grid, block, s);
 }
 
 int walk_occupancy(int prec, int block, int* out) {
   if (prec == 1) return batch_walk_blocks_per_sm<1>(block, out);
   if (prec == 2) return batch_walk_blocks_per_sm<2>(block, out);
+  if (prec == 3) return batch_walk_blocks_per_sm<3>(block, out);
   return batch_walk_blocks_per_sm<0>(block, out);
 }
 

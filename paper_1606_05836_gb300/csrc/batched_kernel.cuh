@@ -83,8 +83,8 @@ __device__ __forceinline__ void batch_walk_n(int n, const double2* Acol, const d
   switch (n) {
 #define PERM_BCASE(N)                                                                              \
   case N:                                                                                          \
-    walk_range<N, PREC, TUNE, true>(Acol, Step, nullptr, nullptr, 0, N, glynn ? KIND_GLYNN : KIND_RYSER, kb, ke, \
-                                    CH, nz, ar, ai, cr, ci);                                                    \
+    walk_range<N, PREC, TUNE, true>(Acol, Step, nullptr, nullptr, nullptr, nullptr, N,                     \
+                                    glynn ? KIND_GLYNN : KIND_RYSER, kb, ke, CH, nz, ar, ai, cr, ci);         \
     break;
     PERM_BCASE(1) PERM_BCASE(2) PERM_BCASE(3) PERM_BCASE(4) PERM_BCASE(5) PERM_BCASE(6) PERM_BCASE(7)
     PERM_BCASE(8) PERM_BCASE(9) PERM_BCASE(10) PERM_BCASE(11) PERM_BCASE(12) PERM_BCASE(13) PERM_BCASE(14)

@@ -287,14 +287,28 @@ __device__ __forceinline__ double2 ldcol(const double2* p) {
 // vector Xb), coef_b = [bit b] over the first n-1 columns); every other step
 // adds +-Step[b], b = ctz(k).  Columns are `stride` complex numbers apart.
 // GLOBAL selects read-only global loads instead of shared-memory loads.
+// Per-thread (sum, compensation) -> normalised double-double.
+template <int PREC>
+__device__ __forceinline__ void acc_to_dd(double ar, double ai, double cr, double ci, dd& sr, dd& si) {
+  if (PREC == 1 || PREC == 2) {
+    sr = dd_add(dd{ar, 0.0}, dd{cr, 0.0});
+    si = dd_add(dd{ai, 0.0}, dd{ci, 0.0});
+  } else {
+    sr = dd{ar, 0.0};
+    si = dd{ai, 0.0};
+  }
+}
+
 // KIND_GLYNN_MULT: Acol holds the g distinct columns, Step the doubled free
-// columns (by free index), mi the column structure and cls the class; [kb, ke)
-// are Gray indices of the free columns within that class.
+// columns (by free index) and mi the column structure; [kb, ke) are indices
+// K = class * 2^nfree + free-column Gray index.  A class boundary ends a chunk
+// (so no lane walks a second segment alone), and each chunk's sum is added to
+// (tot_r, tot_i) times its class weight.
 template <int N, int PREC, int TUNE, bool GLOBAL>
 __device__ __forceinline__ void walk_range(const double2* __restrict__ Acol, const double2* __restrict__ Step,
-                                           const double2* __restrict__ Xb, const MultInfo* mi, long long cls,
-                                           int stride, int kind, uint64_t kb, uint64_t ke, uint64_t CH, double nz,
-                                           double& ar, double& ai, double& cr, double& ci) {
+                                           const double2* __restrict__ Xb, const MultInfo* mi, dd* tot_r,
+                                           dd* tot_i, int stride, int kind, uint64_t kb, uint64_t ke, uint64_t CH,
+                                           double nz, double& ar, double& ai, double& cr, double& ci) {
   const bool glynn = (kind == KIND_GLYNN);
   const bool multk = (kind == KIND_GLYNN_MULT);
   const bool glynn_signs = glynn || multk;
@@ -303,9 +317,19 @@ __device__ __forceinline__ void walk_range(const double2* __restrict__ Acol, con
   // Ryser: a set bit means the column is in S (add a when it turns on).
   const unsigned long long on_mask = glynn_signs ? 0x8000000000000000ull : 0ull;
   const int ncols = (kind == KIND_RYSER_NW) ? N - 1 : (multk ? mi->g : N);
-  for (uint64_t c0 = kb; c0 < ke; c0 += CH) {
-    const uint64_t c1 = (ke - c0 > CH) ? c0 + CH : ke;
-    uint64_t g = c0 ^ (c0 >> 1);
+  // index within a class of the repeated-column expansion (the whole index otherwise)
+  const uint64_t lmask = multk ? ((1ull << mi->nfree) - 1ull) : ~0ull;
+  for (uint64_t c0 = kb; c0 < ke;) {
+    uint64_t c1 = (ke - c0 > CH) ? c0 + CH : ke;
+    long long cls = 0;
+    if (multk) {
+      cls = (long long)(c0 >> mi->nfree);
+      const uint64_t bnd = ((uint64_t)cls + 1) << mi->nfree;
+      if (c1 > bnd) c1 = bnd;
+      ar = ai = cr = ci = 0.0;  // this chunk's sum, weighted below
+    }
+    const uint64_t gidx = c0 & lmask;
+    uint64_t g = gidx ^ (gidx >> 1);
     double vr[N], vi[N];
     // exact row sums at the chunk start: v_i = base_i + sum_j coef_j a_ij
     if (has_base) {
@@ -317,7 +341,10 @@ __device__ __forceinline__ void walk_range(const double2* __restrict__ Acol, con
       }
     } else {
 #pragma unroll
-      for (int i = 0; i < N; i++) { vr[i] = 0.0; vi[i] = 0.0; }
+      for (int i = 0; i < N; i++) {
+        vr[i] = 0.0;
+        vi[i] = 0.0;
+      }
     }
 #pragma unroll 1
     for (int j = 0; j < ncols; j++) {
@@ -343,8 +370,8 @@ __device__ __forceinline__ void walk_range(const double2* __restrict__ Acol, con
     uint64_t k = c0;
 #pragma unroll 1
     while (true) {
-      // term sign (prod delta) = (-1)^popcount(g(k)) = (-1)^(k & 1)
-      const unsigned long long smask = (k & 1ull) << 63;
+      // term sign (prod delta) = (-1)^popcount(g) = (-1)^(index & 1)
+      const unsigned long long smask = ((k & lmask) & 1ull) << 63;
       if (PREC == 0) {
         term_r0<N, TUNE>(vr, vi, smask, ar, ai, nz);
       } else if (PREC == 3) {
@@ -361,7 +388,7 @@ __device__ __forceinline__ void walk_range(const double2* __restrict__ Acol, con
       }
       ++k;
       if (k >= c1) break;
-      // Gray step: bit b = ctz(k) flips
+      // Gray step: bit b = ctz(k) flips (k is not a class start inside a chunk)
       const int b = __ffsll((long long)k) - 1;
       g ^= 1ull << b;
       // negative iff (Glynn and the bit turned on) or (Ryser and it turned off)
@@ -384,8 +411,16 @@ __device__ __forceinline__ void walk_range(const double2* __restrict__ Acol, con
         }
       }
     }
+    if (multk) {
+      // the chunk lies in one class: add its sum times the class weight
+      dd pr, pi;
+      acc_to_dd<PREC>(ar, ai, cr, ci, pr, pi);
+      const double w = mult_class_weight(*mi, cls);
+      *tot_r = dd_add(*tot_r, dd{pr.hi * w, pr.lo * w});
+      *tot_i = dd_add(*tot_i, dd{pi.hi * w, pi.lo * w});
+    }
+    c0 = c1;
   }
-
 }
 
 // Warp butterfly sum of double-double pairs (every lane ends with the same sum).
@@ -399,16 +434,5 @@ __device__ __forceinline__ void warp_sum_dd(dd& sr, dd& si) {
   }
 }
 
-// Per-thread (sum, compensation) -> normalised double-double.
-template <int PREC>
-__device__ __forceinline__ void acc_to_dd(double ar, double ai, double cr, double ci, dd& sr, dd& si) {
-  if (PREC == 1 || PREC == 2) {
-    sr = dd_add(dd{ar, 0.0}, dd{cr, 0.0});
-    si = dd_add(dd{ai, 0.0}, dd{ci, 0.0});
-  } else {
-    sr = dd{ar, 0.0};
-    si = dd{ai, 0.0};
-  }
-}
 
 }  // namespace permk

@@ -160,28 +160,13 @@ __global__ void __launch_bounds__(256, 1) fwd_kernel(FwdArgs a) {
 
   dd sr, si;
   if (a.kind == KIND_GLYNN_MULT) {
-    // split the range at class boundaries; each class's sum times its weight
-    const int f = a.mult.nfree;
     sr = dd{0.0, 0.0};
     si = dd{0.0, 0.0};
-    uint64_t K = kb;
-    while (K < ke) {
-      const long long cls = (long long)(K >> f);
-      const uint64_t next = ((uint64_t)cls + 1) << f;
-      const uint64_t seg_end = next < ke ? next : ke;
-      const uint64_t lb = K & ((1ull << f) - 1);
-      double gr = 0.0, gi = 0.0, hr = 0.0, hi = 0.0;
-      walk_range<N, PREC, TUNE, false>(Acol, Step, nullptr, &a.mult, cls, NP, a.kind, lb, lb + (seg_end - K), CH, nz,
-                                       gr, gi, hr, hi);
-      dd pr, pi;
-      acc_to_dd<PREC>(gr, gi, hr, hi, pr, pi);
-      const double w = mult_class_weight(a.mult, cls);
-      sr = dd_add(sr, dd{pr.hi * w, pr.lo * w});
-      si = dd_add(si, dd{pi.hi * w, pi.lo * w});
-      K = seg_end;
-    }
+    walk_range<N, PREC, TUNE, false>(Acol, Step, nullptr, &a.mult, &sr, &si, NP, a.kind, kb, ke, CH, nz, ar, ai, cr,
+                                     ci);
   } else {
-    walk_range<N, PREC, TUNE, false>(Acol, Step, Xb, nullptr, 0, NP, a.kind, kb, ke, CH, nz, ar, ai, cr, ci);
+    walk_range<N, PREC, TUNE, false>(Acol, Step, Xb, nullptr, nullptr, nullptr, NP, a.kind, kb, ke, CH, nz, ar, ai,
+                                     cr, ci);
     acc_to_dd<PREC>(ar, ai, cr, ci, sr, si);
   }
 

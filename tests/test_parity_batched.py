@@ -31,8 +31,8 @@ def _mixed(count, n_lo, n_hi, seed):
 def test_batched_small_mixed_all_rungs(pg, method):
     mats = _mixed(48, 1, 14, 1)
     want = [oracle.perm_def(A) if A.shape[0] <= 8 else oracle.ryser(A) for A in mats]
-    tol = {"fp64": REL_TOL, "fp64_dd": REL_TOL, "fp32p_dd": 1e-4 if method == "glynn" else 1e-2}
-    for prec in ("fp64", "fp64_dd", "fp32p_dd"):
+    tol = {"fp64": REL_TOL, "fp64_dd": REL_TOL, "fp32p_dd": 1e-4 if method == "glynn" else 1e-2, "fp64_df": REL_TOL}
+    for prec in ("fp64", "fp64_dd", "fp32p_dd", "fp64_df"):
         per, _ = pg.batched(mats, method=method, prec=prec)
         got = per.cpu().numpy()
         for i, w in enumerate(want):

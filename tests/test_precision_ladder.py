@@ -9,6 +9,7 @@ quad Gray-order Glynn oracle (complex inputs) and the exact int128 Ryser oracle
 import importlib.util
 import os
 
+import numpy as np
 import pytest
 
 from conftest import GOLDEN, read_tsv
@@ -73,3 +74,26 @@ def test_precision_ladder(pg):
     # 10^7-10^9 apart)
     big = [e for kind, n, e in results if kind == "ones_noise" and n == 28][0]
     assert big[("ryser", "fp64")] > 1e3 * max(big[("glynn", "fp64")], 1e-16)
+
+
+def test_summation_order_study_ryser_allones(pg):
+    """The paper's order study (Ryser on all-ones, errors for several orders of
+    the additions): this decomposition's order — short contiguous per-thread
+    runs in Gray order, then a fixed double-double tree — lands with the paper's
+    "original" and "merging" orders, within two decades, at every n of the table
+    we can check quickly."""
+    import math
+    from fractions import Fraction
+    paper = {int(r["n"]): r for r in read_tsv("ryser_order_allones.tsv")}
+    print()
+    for n in (20, 24, 26, 28):
+        dA = to_dev(np.ones((n, n), dtype=np.complex128))
+        exact = math.factorial(n)
+        e_def = float(abs(Fraction(val(pg.ryser(dA)).real) - exact) / exact)
+        p = paper[n]
+        print("n=%d ours %.2e (paper original %s, merging %s, separating %s, random %s)" % (
+            n, e_def, p["original"], p["merging"], p["separating"], p["random"]))
+        lo = min(float(p["original"]), float(p["merging"]))
+        hi = max(float(p["original"]), float(p["merging"]))
+        assert lo / 100 <= e_def <= hi * 100, (n, e_def)
+        assert e_def < float(p["separating"]) and e_def < float(p["random"])

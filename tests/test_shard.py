@@ -92,3 +92,41 @@ def test_logical_shards_on_one_gpu():
     per = complex(re[0] + re[1], im[0] + im[1]) / float(1 << 25)
     assert abs(per - full) <= 1e-12 * abs(full)
     assert abs(sharded_permanent(26, "glynn", fn, 0, 1) - full) <= 1e-12 * abs(full)
+
+
+def _dying_rank_main(rank, world, port, q):
+    import datetime
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    A = S.gaussian(9, 78)
+    if rank == 1:
+        os._exit(0)  # this rank fails before the exchange of partials
+
+    def partial(kb, ke):
+        r = oracle.glynn_range(A, kb, ke, gray=True, threads=1)
+        return r.hi, r.lo
+
+    try:
+        sharded_permanent(9, "glynn", partial, rank, world)
+        q.put("no error")
+    except Exception as e:  # the surviving rank must see an error, not hang
+        q.put("error: %s" % type(e).__name__)
+
+
+def test_a_dead_rank_fails_the_exchange_instead_of_hanging():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dying_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(90)
+    alive = [p for p in procs if p.is_alive()]
+    for p in alive:
+        p.kill()
+    assert not alive, "a rank hung"
+    msg = q.get(timeout=10)
+    assert msg.startswith("error"), msg
