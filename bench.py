@@ -57,6 +57,7 @@ def parse_args():
     ap.add_argument("--form", choices=["sweep", "batched", "adjoint"], default="sweep",
                     help="sweep = the metric above (default); batched / adjoint time only that form "
                          "(for profiling) and print its own JSON line")
+    ap.add_argument("--batched-count", type=int, default=4096)
     ap.add_argument("--adjoint-n", type=int, default=24)
     ap.add_argument("--adjoint-batch", type=int, default=64)
     return ap.parse_args()
@@ -331,6 +332,11 @@ def measure_forms(dev, plain_rate):
     lap = float(np.max(np.abs(np.sum(A0 * M[0].cpu().numpy(), axis=1) - P0)) / abs(P0))
     forms["adjoint_64_n24"] = {"terms_per_s": 64 * 2 ** 23 / tg, "s": tg, "cost_vs_plain_same_batch": tg / tf,
                                "laplace_identity_rel_err": lap}
+    # adjoint at n = 32 on a batch of 2 (64 would take minutes)
+    G32 = torch.as_tensor(np.stack([S.gaussian(32, b) for b in range(2)])).to(dev)
+    tg32 = timed(lambda: pg.grad(G32))
+    tf32 = timed(lambda: [pg.glynn(G32[b]) for b in range(2)])
+    forms["adjoint_2_n32"] = {"terms_per_s": 2 * 2 ** 31 / tg32, "s": tg32, "cost_vs_plain_same_batch": tg32 / tf32}
     return forms
 
 
@@ -521,7 +527,7 @@ def run_single_form(args):
 
         from paper_1606_05836_gb300 import batch as B
         U = S.haar_unitary(1000, 0)
-        mats, ns, rows, cols, collide = S.batch_patterns(U, 4096, 8, 24, 1)
+        mats, ns, rows, cols, collide = S.batch_patterns(U, args.batched_count, 8, 24, 1)
         scale = [1.0 / float(np.prod([math.factorial(int(x)) for x in np.bincount(c)])) for c in cols]
         bp = B.BatchedPermanents(mats, method="glynn", scale=scale)
         for _ in range(args.warmup):
