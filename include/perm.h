@@ -187,9 +187,9 @@ int prob_sample(const perm_c128* dU, int m, int ldu, const int32_t* hS, const in
  * dMinor:    nullable [batch][n][n] dPer/da_ij = Per(A_b without row i, column j).
  * dGradAbs2: nullable [batch][n][n] 2 Per conj(dPer/da_ij) = d|Per|^2/dRe a_ij
  *            + i d|Per|^2/dIm a_ij (PyTorch's convention for a real loss).
- * dWork:     256-byte-aligned, perm_grad_workspace_size() bytes: per lane an n x n
- *            accumulator and snapshot (O(grid x 128 x 2 n^2 x 16) bytes, e.g.
- *            0.64 GB at n = 32).  The batch runs item after item on `stream`.
+ * dWork:     256-byte-aligned, perm_grad_workspace_size() bytes: per lane one n x n
+ *            complex accumulator (grid x 128 x n^2 x 16 bytes, e.g. 0.32 GB at
+ *            n = 32).  The batch runs item after item on `stream`.
  * 1 <= n <= PERM_GRAD_MAX_N (n = 0 gives Per = 1, no derivatives). */
 #define PERM_GRAD_MAX_N 32
 size_t perm_grad_workspace_size(int n, const perm_opts* opts);
@@ -222,6 +222,58 @@ int perm_grad(const perm_c128* dA, int n, int lda, int batch, int64_t strideA, p
 #define PERM_NOALLOC_MAX_BLOCKS 4096
 #define PERM_NOALLOC_SCRATCH_BYTES (256 + 32 * PERM_NOALLOC_MAX_BLOCKS)
 int perm_glynn_noalloc(const perm_c128* dA, int n, int lda, perm_c128* dOut, const perm_opts* opts, void* stream);
+
+/* --- row minors and boson-sampling draws ----------------------------------- */
+
+/* The k permanents m_j = Per(M without column j) of (k-1) x k matrices M, in one
+ * Gray-code pass per matrix: appending a free last row x to M, Supp. Eq. (S2)
+ * of arXiv 1606.05836 is linear in x and m_j is the coefficient of x_j,
+ *     m_j = 2^-(k-1) sum_delta (prod delta) delta_j prod_{i<k-1} (sum_l delta_l M_il).
+ * (The paper has no such routine; the boson sampler below needs it.)  Plain FP64.
+ *
+ * dM:    batch matrices (device, complex128, row-major, k-1 rows of k entries,
+ *        row stride ldm >= k); matrix b at dM + b*strideM elements.
+ * dOut:  [batch][k] device results.
+ * dWork: 256-byte-aligned, perm_row_minors_workspace_size(k, batch) bytes
+ *        (per block partials: O(batch x blocks per item x k x 32) bytes).
+ * 1 <= k <= PERM_MINORS_MAX_K; k = 1 gives m_0 = 1 (the empty permanent).
+ * Asynchronous on `stream`; errors as for perm_glynn. */
+#define PERM_MINORS_MAX_K 32
+size_t perm_row_minors_workspace_size(int k, int batch, const perm_opts* opts);
+int perm_row_minors(const perm_c128* dM, int k, int ldm, int batch, int64_t strideM, perm_c128* dOut,
+                    void* dWork, size_t workBytes, const perm_opts* opts, void* stream);
+
+/* Draws output patterns of Eq. (1) of arXiv 1606.05836 for n photons in n
+ * distinct input modes, by the chain rule of Clifford and Clifford (SODA 2018):
+ * the paper only bounds the cost of a draw by that of one permanent.  With
+ * A[l][j] = U[in(alpha_j)][l] (U[i][j]: amplitude from input mode i to output
+ * mode j, as for prob_sample), step k = 1..n weighs every output mode l by
+ *     w_k(l) = |Per(A[(r_1..r_{k-1}, l), (0..k-1)])|^2
+ *            = |sum_j A[l][j] Per(A[(r_1..r_{k-1}), (0..k-1) without j])|^2
+ * (the k minors by the kernel of perm_row_minors, read straight from U) and
+ * takes r_k = the first mode whose running sum of w_k, accumulated in mode order,
+ * exceeds u_k * W, W = that sum over all m modes; if rounding leaves u_k W at or
+ * above every running sum, the last mode of positive weight.
+ *
+ * dU:       the m x m unitary (device, row-major, ldu >= m).
+ * hInputs:  host, n distinct input modes in [0, m).
+ * dAlpha:   device [nsamples][n] int32, each row a permutation of 0..n-1 (the
+ *           draw's random photon order), caller-drawn uniformly.
+ * dUnif:    device [nsamples][n] doubles in [0, 1) (the draw's uniforms).
+ * dR:       device [nsamples][n] int32 out: r_1..r_n (output modes, draw order;
+ *           the pattern is their multiset).  A draw whose alpha or uniforms are
+ *           invalid, or that meets a step of zero or non-finite total weight,
+ *           has all n entries -1.
+ * dWork:    256-byte-aligned, boson_sample_workspace_size(m, n, nsamples) bytes
+ *           (O(nsamples x (16 m + 8 n) + partials)).
+ * 1 <= n <= BOSON_SAMPLE_MAX_N, n <= m.  2n - 1 kernel launches, all on
+ * `stream`, no host synchronisation (the call may be captured in a CUDA graph
+ * once the workspace exists). */
+#define BOSON_SAMPLE_MAX_N 32
+size_t boson_sample_workspace_size(int m, int n, int nsamples, const perm_opts* opts);
+int boson_sample(const perm_c128* dU, int m, int ldu, int n, const int32_t* hInputs, int nsamples,
+                 const int32_t* dAlpha, const double* dUnif, int32_t* dR, void* dWork, size_t workBytes,
+                 const perm_opts* opts, void* stream);
 
 /* --- diagnostics ----------------------------------------------------------- */
 

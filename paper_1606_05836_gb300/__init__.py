@@ -17,6 +17,9 @@ Functions mirror the C entry points:
 * :func:`prob` -- Eq. (1): |Per(U_ST)|^2 / (prod s_i! prod t_j!) for one (S, T)
 * :func:`grad`, :class:`PermAbs2` -- the adjoint: dPer/dA and d|Per|^2/dA in the
   same Gray-code pass, behind a torch.autograd.Function
+* :func:`row_minors` -- the k permanents Per(M without column j) of a (k-1) x k matrix
+* :class:`BosonSampler`, :func:`boson_sample` -- draws from Eq. (1) by the chain rule
+  over the photons, each step one row-minor pass (CUDA-graph capture)
 """
 from __future__ import annotations
 
@@ -188,3 +191,4 @@ def ryser_range(A, k_begin: int, k_end: int, prec="fp64", chunk_log2=0, block=0,
 
 from .batch import BatchedPermanents, batched  # noqa: E402
 from .grad import PermAbs2, grad  # noqa: E402
+from .sampler import BosonSampler, boson_sample, row_minors  # noqa: E402

@@ -32,6 +32,10 @@ EXPORTS = (
     "perm_grad_workspace_size",
     "perm_grad",
     "perm_glynn_noalloc",
+    "perm_row_minors_workspace_size",
+    "perm_row_minors",
+    "boson_sample_workspace_size",
+    "boson_sample",
     "perm_strerror",
     "perm_last_cuda_error",
     "perm_version",
@@ -94,6 +98,14 @@ def load(path: str | None = None):
     lib.perm_grad.restype = i32
     lib.perm_glynn_noalloc.argtypes = [vp, i32, i32, vp, op, vp]
     lib.perm_glynn_noalloc.restype = i32
+    lib.perm_row_minors_workspace_size.argtypes = [i32, i32, op]
+    lib.perm_row_minors_workspace_size.restype = sz
+    lib.perm_row_minors.argtypes = [vp, i32, i32, i32, ctypes.c_int64, vp, vp, sz, op, vp]
+    lib.perm_row_minors.restype = i32
+    lib.boson_sample_workspace_size.argtypes = [i32, i32, i32, op]
+    lib.boson_sample_workspace_size.restype = sz
+    lib.boson_sample.argtypes = [vp, i32, i32, i32, ctypes.POINTER(ctypes.c_int32), i32, vp, vp, vp, vp, sz, op, vp]
+    lib.boson_sample.restype = i32
     lib.perm_strerror.argtypes = [i32]
     lib.perm_strerror.restype = ctypes.c_char_p
     lib.perm_last_cuda_error.argtypes = []

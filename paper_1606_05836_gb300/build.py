@@ -31,6 +31,7 @@ MULTI = {
     "fwd_inst.cu": ["-DPERM_PART=%d" % p for p in range(8)],
     "batched_inst.cu": ["-DPERM_PREC=%d" % p for p in range(4)],
     "grad_inst.cu": ["-DPERM_PART=%d" % p for p in range(4)],
+    "minors_inst.cu": ["-DPERM_PART=%d" % p for p in range(2)],
 }
 
 

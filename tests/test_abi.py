@@ -22,7 +22,7 @@ def declared_functions():
         text = re.sub(r"//[^\n]*", "", text)
         for m in re.finditer(r"\b([A-Za-z_][A-Za-z0-9_]*)\s*\(", text):
             name = m.group(1)
-            if name.startswith(("perm_", "prob_")) and not name.startswith("perm_c128"):
+            if name.startswith(("perm_", "prob_", "boson_")) and not name.startswith("perm_c128"):
                 names.append(name)
     return sorted(set(names))
 
