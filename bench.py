@@ -49,17 +49,20 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n-list", default="24,28,32", help="matrix sizes of the sweep")
     ap.add_argument("--kinds", default="glynn,ryser")
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp64_dd", "fp32p_dd"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp64_dd", "fp32p_dd", "fp64_df", "fp32x2"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / compensated / adjoint forms")
-    ap.add_argument("--form", choices=["sweep", "batched", "adjoint"], default="sweep",
-                    help="sweep = the metric above (default); batched / adjoint time only that form "
-                         "(for profiling) and print its own JSON line")
+    ap.add_argument("--form", choices=["sweep", "batched", "adjoint", "sampler"], default="sweep",
+                    help="sweep = the metric above (default); batched / adjoint / sampler time only that "
+                         "form (for profiling) and print its own JSON line")
     ap.add_argument("--batched-count", type=int, default=4096)
     ap.add_argument("--adjoint-n", type=int, default=24)
     ap.add_argument("--adjoint-batch", type=int, default=64)
+    ap.add_argument("--sampler-m", type=int, default=1000)
+    ap.add_argument("--sampler-n", type=int, default=24)
+    ap.add_argument("--sampler-count", type=int, default=16)
     return ap.parse_args()
 
 
@@ -272,10 +275,11 @@ def measure_forms(dev, plain_rate):
     import numpy as np
     import torch
 
-    import oracle
     import paper_1606_05836_gb300 as pg
     import synthetic as S
     from paper_1606_05836_gb300 import batch as B
+
+    refs = bench_refs()
 
     def timed(fn, reps=1):
         best = None
@@ -294,11 +298,11 @@ def measure_forms(dev, plain_rate):
     A32 = torch.as_tensor(S.gaussian(32, 0)).to(dev)
     A20h = S.gaussian(20, 0)
     A20 = torch.as_tensor(A20h).to(dev)
-    want20 = oracle.glynn(A20h)
-    for prec in ("fp64", "fp64_dd", "fp32p_dd", "fp64_df"):
+    r20 = refs["glynn_gaussian_n20"]
+    for prec in ("fp64", "fp64_dd", "fp32p_dd", "fp64_df", "fp32x2"):
         pg.glynn(A32, prec=prec)
         t = timed(lambda: pg.glynn(A32, prec=prec))
-        err = want20.rel_err(complex(pg.glynn(A20, prec=prec).cpu().item()))
+        err = ref_rel_err(r20, A20h, complex(pg.glynn(A20, prec=prec).cpu().item()))
         forms["glynn_n32_" + prec] = {"terms_per_s": 2 ** 31 / t, "vs_plain_glynn": None, "rel_err_n20_vs_oracle": err}
     base = forms["glynn_n32_fp64"]["terms_per_s"]
     for k in list(forms):
@@ -314,9 +318,12 @@ def measure_forms(dev, plain_rate):
     t = timed(bp.replay, reps=3)
     terms = int(sum(2 ** (int(n) - 1) for n in ns))
     per = bp.out.cpu().numpy()
-    # sampled parity of the batch against the oracle (items with n <= 16)
-    small = [i for i in range(len(mats)) if ns[i] <= 14][:8]
-    berr = max(oracle.glynn(mats[i]).rel_err(per[i]) for i in small) if small else None
+    # sampled parity of the batched kernel: the 8 stored items (n <= 14) of this batch, with their oracle values
+    items = refs["batched_items"]
+    pick = [unflat(r["matrix"], r["n"], r["n"]) for r in items]
+    per8, _ = pg.batched(pick, method="glynn")
+    per8 = per8.cpu().numpy()
+    berr = max(ref_rel_err(r, pick[i], complex(per8[i])) for i, r in enumerate(items))
     forms["batched_4096_n8-24"] = {"terms_per_s": terms / t, "perms_per_s": len(mats) / t, "s_per_replay": t,
                                    "vs_plain_glynn": terms / t / base, "collision_items": int(collide.sum()),
                                    "tuned": {"unit_log2": tuned["unit_log2"], "block": tuned["block"]},
@@ -337,7 +344,71 @@ def measure_forms(dev, plain_rate):
     tg32 = timed(lambda: pg.grad(G32))
     tf32 = timed(lambda: [pg.glynn(G32[b]) for b in range(2)])
     forms["adjoint_2_n32"] = {"terms_per_s": 2 * 2 ** 31 / tg32, "s": tg32, "cost_vs_plain_same_batch": tg32 / tf32}
+    # row minors of a 31 x 32 matrix in one pass, against the forward kernel at n = 32
+    M32 = torch.as_tensor(S.circular_gaussian((31, 32), 0, 1.0 / 32)).to(dev)
+    pg.row_minors(M32)
+    tm = timed(lambda: pg.row_minors(M32))
+    forms["row_minors_k32"] = {"terms_per_s": 2 ** 31 / tm, "s": tm, "cost_vs_glynn_n32": tm * base / 2 ** 31}
+    # boson-sampling draws: 16 draws of 24 photons in the 1000-mode unitary (one graph replay)
+    m, n, ns = 1000, 24, 16
+    smp, alpha, uu = sampler_case(pg, U, n, ns, 5, dev)
+    smp.capture()
+    smp.replay()
+    ts = timed(smp.replay, reps=2)
+    A24 = torch.as_tensor(S.gaussian(24, 0)).to(dev)
+    pg.glynn(A24)
+    t24 = timed(lambda: pg.glynn(A24), reps=2)
+    # sampled parity: 4 draws of 8 photons in 30 modes against the oracle's stored draws
+    rs = refs["sampler_m30_n8"]
+    U30 = unflat(rs["U"], 30, 30)
+    s30, a30, u30 = sampler_case(pg, U30, 8, 4, 6, dev)
+    got = s30.run().cpu().numpy()
+    same = "%d/4" % sum(int(list(got[i]) == rs["draws"][i]) for i in range(4))
+    forms["boson_sample_m1000_n24_x16"] = {"draws_per_s": ns / ts, "s_per_replay": ts,
+                                           "terms_per_s": ns * (2 ** n - 2) / ts,
+                                           "cost_per_draw_in_glynn_n24": ts / ns / t24,
+                                           "launches_per_replay": 2 * n - 1,
+                                           "draws_equal_oracle_m30_n8": same}
     return forms
+
+
+def bench_refs():
+    """Oracle values for the forms' parity figures, written by tests/golden/make_bench_refs.py."""
+    with open(os.path.join(ROOT, "tests", "golden", "bench_refs.json")) as f:
+        return json.load(f)
+
+
+def input_digest(A) -> str:
+    import hashlib
+
+    import numpy as np
+    return hashlib.sha256(np.ascontiguousarray(A).tobytes()).hexdigest()[:16]
+
+
+def unflat(v, rows: int, cols: int):
+    import numpy as np
+    return np.asarray(v, dtype=np.float64).view(np.complex128).reshape(rows, cols)
+
+
+def ref_rel_err(ref, A, got: complex):
+    """|got - P| / |P| against a stored oracle value; None if the input was not regenerated bit for bit."""
+    if ref["sha"] != input_digest(A):
+        return None
+    rh, rl, ih, il = ref["value"]
+    d = complex((got.real - rh) - rl, (got.imag - ih) - il)
+    return abs(d) / abs(complex(rh + rl, ih + il))
+
+
+def sampler_case(pg, U, n, ns, seed, dev):
+    """A BosonSampler on U (numpy) with photons in modes 0..n-1 and seeded draws loaded."""
+    import torch
+
+    import synthetic as S
+
+    alpha, uu = S.sampler_draws(n, ns, seed)
+    smp = pg.BosonSampler(torch.as_tensor(U).to(dev), list(range(n)), ns)
+    smp.load(torch.as_tensor(alpha).to(dev), torch.as_tensor(uu).to(dev))
+    return smp, alpha, uu
 
 
 # ---------------------------------------------------------------------------
@@ -507,7 +578,22 @@ def run_single_form(args):
     import synthetic as S
 
     dev = torch.device("cuda", 0)
-    if args.form == "adjoint":
+    if args.form == "sampler":
+        m, n, ns = args.sampler_m, args.sampler_n, args.sampler_count
+        smp, _, _ = sampler_case(pg, S.haar_unitary(m, 0), n, ns, 5, dev)
+        for _ in range(args.warmup):
+            smp.run()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            smp.run()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        t = e0.elapsed_time(e1) / 1e3
+        print(json.dumps({"form": "sampler", "m": m, "n": n, "count": ns, "steps": args.steps,
+                          "draws_per_s": args.steps * ns / t}), flush=True)
+    elif args.form == "adjoint":
         n, b = args.adjoint_n, args.adjoint_batch
         G = torch.as_tensor(np.stack([S.gaussian(n, i) for i in range(b)])).to(dev)
         for _ in range(args.warmup):

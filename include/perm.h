@@ -56,22 +56,25 @@ typedef enum {
   PERM_ETIMEOUT = -6    /* reserved: a bounded wait ran out */
 } perm_status;
 
-/* Precision ladder.  FP64 is used in every rung for the Gray-code row-sum
- * updates, the row sums recomputed at each chunk start and the cross-block
- * reduction. */
+/* Precision ladder.  FP64 is used in every rung for the row sums recomputed at
+ * each chunk start, the accumulation of the terms and the cross-block reduction;
+ * R0-R3 also update the row sums in FP64 at every Gray step. */
 typedef enum {
   PERM_FP64 = 0,    /* R0: FP64 products, FP64 accumulation of the terms */
   PERM_FP64_DD = 1, /* R1: FP64 products, double-double accumulation of the terms */
   PERM_FP32P_DD = 2, /* R2: FP32 n-way products of the FP64 row sums, double-double accumulation */
-  PERM_FP64_DF = 3   /* R3: the FP64 row sums split exactly into FP32 pairs and multiplied in
-                        double-float arithmetic on the FP32 pipe (~48-bit products), FP64
-                        accumulation */
+  PERM_FP64_DF = 3,  /* R3: the FP64 row sums split into FP32 pairs (~48 bits) and multiplied in
+                        double-float arithmetic on the FP32 pipe, FP64 accumulation */
+  PERM_FP32X2 = 4    /* R4: double-float (FP32 pair, ~48-bit) row sums updated at every step and
+                        double-float products, all on the FP32 pipe; exact FP64 row sums at each
+                        chunk start (default every 2^10 steps), FP64 accumulation.  Glynn only
+                        (perm_glynn, perm_glynn_range, perm_glynn_noalloc); EINVAL elsewhere */
 } perm_prec;
 
 /* Launch options; pass NULL for the defaults (every field 0 = default). */
 typedef struct {
   int prec;       /* perm_prec */
-  int chunk_log2; /* row sums are recomputed from scratch every 2^chunk_log2 steps (default 12, 1..30) */
+  int chunk_log2; /* row sums are recomputed from scratch every 2^chunk_log2 steps (default 12; R4: 10; 1..30) */
   int block;      /* threads per block (multiple of 32, 32..256; default 128) */
   int grid;       /* blocks (default: SMs x resident blocks per SM) */
   int unit_log2;  /* perm_batched: Gray indices per lane in one work unit, log2 (default 11, 0..30) */

@@ -12,8 +12,9 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "lib", "libperm.so")
 
 PERM_MAX_N = 48
-PERM_FP64, PERM_FP64_DD, PERM_FP32P_DD, PERM_FP64_DF = 0, 1, 2, 3
-PRECISIONS = {"fp64": PERM_FP64, "fp64_dd": PERM_FP64_DD, "fp32p_dd": PERM_FP32P_DD, "fp64_df": PERM_FP64_DF}
+PERM_FP64, PERM_FP64_DD, PERM_FP32P_DD, PERM_FP64_DF, PERM_FP32X2 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": PERM_FP64, "fp64_dd": PERM_FP64_DD, "fp32p_dd": PERM_FP32P_DD, "fp64_df": PERM_FP64_DF,
+              "fp32x2": PERM_FP32X2}
 
 # every symbol include/perm.h declares
 EXPORTS = (

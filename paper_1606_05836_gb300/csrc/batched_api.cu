@@ -255,6 +255,7 @@ size_t perm_batched_workspace_size(int count, const int32_t* hN, int method, con
 int perm_batched(const perm_c128* dPacked, const int64_t* dOffsets, const int32_t* dN, const int32_t* hN, int count,
                  int method, const double* dScale, perm_c128* dOut, double* dProb, void* dWork, size_t workBytes,
                  const perm_opts* opts, void* stream) {
+  permk::NvtxRange nvtx_range("perm_batched");
   cudaStream_t s = (cudaStream_t)stream;
   if (count < 0 || (method != 0 && method != 1)) return PERM_EINVAL;
   if (count == 0) return PERM_OK;

@@ -270,6 +270,90 @@ __device__ __forceinline__ void prod_df(const double (&vr)[N], const double (&vi
   pi = f32_to_f64_int(ai.h) + f32_to_f64_int(ai.l);
 }
 
+// R4: double-float row sums as well, so the whole walk runs on the FP32 pipe.
+// Two-sum of the high parts, low parts added, renormalised (Dekker's double-
+// length addition); the _rn intrinsics keep it from being contracted.
+__device__ __forceinline__ df df_add(const df a, const df b) {
+  const float s = __fadd_rn(a.h, b.h);
+  const float bb = __fsub_rn(s, a.h);
+  const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+  const float t = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  const float h = __fadd_rn(s, t);
+  return df{h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+
+// Glynn walk over [kb, ke) with double-float row sums: exact FP64 row sums at
+// every chunk start (from Acol), split into double-float; each step adds or
+// subtracts the flipped doubled column (StepF, double-float (re h, re l, im h,
+// im l)); the double-float product goes to FP64 exactly and is accumulated in FP64.
+template <int N>
+__device__ __forceinline__ void walk_range_df(const double2* __restrict__ Acol, const float4* __restrict__ StepF,
+                                              int stride, uint64_t kb, uint64_t ke, uint64_t CH, double& ar,
+                                              double& ai) {
+  for (uint64_t c0 = kb; c0 < ke;) {
+    const uint64_t c1 = (ke - c0 > CH) ? c0 + CH : ke;
+    uint64_t g = c0 ^ (c0 >> 1);
+    float rh[N], rl[N], ih[N], il[N];
+    {
+      double vr[N], vi[N];
+#pragma unroll
+      for (int i = 0; i < N; i++) {
+        vr[i] = 0.0;
+        vi[i] = 0.0;
+      }
+#pragma unroll 1
+      for (int j = 0; j < N; j++) {
+        const double coef = (j == 0) ? 1.0 : (((g >> (j - 1)) & 1ull) ? -1.0 : 1.0);
+        const double2* col = Acol + j * stride;
+#pragma unroll
+        for (int i = 0; i < N; i++) {
+          const double2 x = col[i];
+          vr[i] = fma(coef, x.x, vr[i]);
+          vi[i] = fma(coef, x.y, vi[i]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < N; i++) {
+        const df a = f64_to_df(vr[i]), b = f64_to_df(vi[i]);
+        rh[i] = a.h;
+        rl[i] = a.l;
+        ih[i] = b.h;
+        il[i] = b.l;
+      }
+    }
+    uint64_t k = c0;
+#pragma unroll 1
+    while (true) {
+      df pr{rh[0], rl[0]}, pi{ih[0], il[0]};
+#pragma unroll
+      for (int i = 1; i < N; i++) dfc_mul(pr, pi, df{rh[i], rl[i]}, df{ih[i], il[i]});
+      const double xr = f32_to_f64_int(pr.h) + f32_to_f64_int(pr.l);
+      const double xi = f32_to_f64_int(pi.h) + f32_to_f64_int(pi.l);
+      const unsigned long long smask = (k & 1ull) << 63;  // (prod delta) = (-1)^(k & 1)
+      ar += xor_sign(xr, smask);
+      ai += xor_sign(xi, smask);
+      ++k;
+      if (k >= c1) break;
+      const int b = __ffsll((long long)k) - 1;
+      g ^= 1ull << b;
+      // bit now set: delta_{b+2} became -1, subtract 2a; bit now clear: add
+      const float sg = ((g >> b) & 1ull) ? -1.0f : 1.0f;
+      const float4* col = StepF + b * stride;
+#pragma unroll
+      for (int i = 0; i < N; i++) {
+        const float4 x = col[i];
+        const df u = df_add(df{rh[i], rl[i]}, df{__fmul_rn(sg, x.x), __fmul_rn(sg, x.y)});
+        const df v = df_add(df{ih[i], il[i]}, df{__fmul_rn(sg, x.z), __fmul_rn(sg, x.w)});
+        rh[i] = u.h;
+        rl[i] = u.l;
+        ih[i] = v.h;
+        il[i] = v.l;
+      }
+    }
+    c0 = c1;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // one thread's Gray walk over [kb, ke) (steps a2-a5)
 // ---------------------------------------------------------------------------

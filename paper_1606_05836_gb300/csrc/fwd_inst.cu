@@ -48,6 +48,7 @@ int launch_fwd(const FwdArgs& a, int prec, int tune, int grid, int block, cudaSt
   if (prec == 1) return launch_one<N, 1, PERM_DEFAULT_TUNE>(a, grid, block, s);
   if (prec == 2) return launch_one<N, 2, PERM_DEFAULT_TUNE>(a, grid, block, s);
   if (prec == 3) return launch_one<N, 3, PERM_DEFAULT_TUNE>(a, grid, block, s);
+  if (prec == 4) return launch_one<N, 4, PERM_DEFAULT_TUNE>(a, grid, block, s);
   if constexpr (HasTuneVariants<N>::value) {
     switch (tune) {
       case 0: return launch_one<N, 0, 0>(a, grid, block, s);
@@ -65,6 +66,7 @@ int fwd_blocks_per_sm(int prec, int tune, int block, int kind, int* out) {
   if (prec == 1) return occupancy_one<N, 1, PERM_DEFAULT_TUNE>(block, kind, out);
   if (prec == 2) return occupancy_one<N, 2, PERM_DEFAULT_TUNE>(block, kind, out);
   if (prec == 3) return occupancy_one<N, 3, PERM_DEFAULT_TUNE>(block, kind, out);
+  if (prec == 4) return occupancy_one<N, 4, PERM_DEFAULT_TUNE>(block, kind, out);
   if constexpr (HasTuneVariants<N>::value) {
     switch (tune) {
       case 0: return occupancy_one<N, 0, 0>(block, kind, out);

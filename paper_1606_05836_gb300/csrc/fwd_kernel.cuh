@@ -159,7 +159,20 @@ __global__ void __launch_bounds__(256, 1) fwd_kernel(FwdArgs a) {
   double ar = 0.0, ai = 0.0, cr = 0.0, ci = 0.0;  // accumulator and (R1/R2) compensation
 
   dd sr, si;
-  if (a.kind == KIND_GLYNN_MULT) {
+  if constexpr (PREC == 4) {
+    // R4 (Glynn only): the doubled columns to double-float, in place (16 bytes each)
+    float4* StepF = reinterpret_cast<float4*>(Step);
+    for (int idx = threadIdx.x; idx < (N - 1) * N; idx += blockDim.x) {
+      const int b = idx / N, i = idx % N;
+      const double2 v = Step[b * NP + i];
+      const df re = f64_to_df(v.x), im = f64_to_df(v.y);
+      StepF[b * NP + i] = make_float4(re.h, re.l, im.h, im.l);
+    }
+    __syncthreads();
+    walk_range_df<N>(Acol, StepF, NP, kb, ke, CH, ar, ai);
+    sr = dd{ar, 0.0};
+    si = dd{ai, 0.0};
+  } else if (a.kind == KIND_GLYNN_MULT) {
     sr = dd{0.0, 0.0};
     si = dd{0.0, 0.0};
     walk_range<N, PREC, TUNE, false>(Acol, Step, nullptr, &a.mult, &sr, &si, NP, a.kind, kb, ke, CH, nz, ar, ai, cr,

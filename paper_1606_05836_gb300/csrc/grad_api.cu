@@ -160,6 +160,7 @@ size_t perm_grad_workspace_size(int n, const perm_opts* opts) {
 int perm_grad(const perm_c128* dA, int n, int lda, int batch, int64_t strideA, perm_c128* dPerm, double* dAbs2,
               perm_c128* dMinor, perm_c128* dGradAbs2, void* dWork, size_t workBytes, const perm_opts* opts,
               void* stream) {
+  permk::NvtxRange nvtx_range("perm_grad");
   cudaStream_t s = (cudaStream_t)stream;
   if (n < 0 || n > PERM_GRAD_MAX_N) return PERM_ERANGE;
   if (batch < 0) return PERM_EINVAL;

@@ -88,10 +88,11 @@ int sm_count(int* out) {
 
 int read_opts(const perm_opts* o, int* prec, int* chunk_log2, int* block, int* grid) {
   *prec = o ? o->prec : PERM_FP64;
-  *chunk_log2 = (o && o->chunk_log2) ? o->chunk_log2 : 12;
+  // R4 re-splits its double-float row sums from exact FP64 sums more often
+  *chunk_log2 = (o && o->chunk_log2) ? o->chunk_log2 : ((o && o->prec == PERM_FP32X2) ? 10 : 12);
   *block = (o && o->block) ? o->block : 128;
   *grid = o ? o->grid : 0;
-  if (*prec < PERM_FP64 || *prec > PERM_FP64_DF) return PERM_EINVAL;
+  if (*prec < PERM_FP64 || *prec > PERM_FP32X2) return PERM_EINVAL;
   if (*chunk_log2 < 1 || *chunk_log2 > 30) return PERM_EINVAL;
   if (*block < 32 || *block > 256 || (*block & 31)) return PERM_EINVAL;
   if (*grid < 0) return PERM_EINVAL;
@@ -115,6 +116,7 @@ int plan_fwd(int n, int kind, uint64_t range, const perm_opts* o, Plan* p) {
   int grid_opt = 0;
   int st = read_opts(o, &p->prec, &p->chunk_log2, &p->block, &grid_opt);
   if (st) return st;
+  if (p->prec == PERM_FP32X2 && kind != permk::KIND_GLYNN) return PERM_EINVAL;  // R4 is a Glynn walk
   p->tune = tune_override();
   if (grid_opt > 0) {
     p->grid = grid_opt;
@@ -331,30 +333,35 @@ size_t perm_workspace_size(int n, const perm_opts* opts) {
 
 int perm_glynn(const perm_c128* dA, int n, int lda, perm_c128* dOut, void* dWork, size_t workBytes,
                const perm_opts* opts, void* stream) {
+  permk::NvtxRange nvtx_range("perm_glynn");
   const uint64_t full = (n >= 1 && n <= PERM_MAX_N) ? (1ull << (n - 1)) : 0;
   return run_fwd(dA, n, lda, permk::KIND_GLYNN, 0, full, 0, dOut, dWork, workBytes, opts, stream);
 }
 
 int perm_ryser(const perm_c128* dA, int n, int lda, perm_c128* dOut, void* dWork, size_t workBytes,
                const perm_opts* opts, void* stream) {
+  permk::NvtxRange nvtx_range("perm_ryser");
   const uint64_t full = (n >= 1 && n <= PERM_MAX_N) ? (1ull << n) : 0;
   return run_fwd(dA, n, lda, permk::KIND_RYSER, 0, full, 0, dOut, dWork, workBytes, opts, stream);
 }
 
 int perm_ryser_nw(const perm_c128* dA, int n, int lda, perm_c128* dOut, void* dWork, size_t workBytes,
                   const perm_opts* opts, void* stream) {
+  permk::NvtxRange nvtx_range("perm_ryser_nw");
   const uint64_t full = (n >= 1 && n <= PERM_MAX_N) ? (1ull << (n - 1)) : 0;
   return run_fwd(dA, n, lda, permk::KIND_RYSER_NW, 0, full, 0, dOut, dWork, workBytes, opts, stream);
 }
 
 int perm_glynn_range(const perm_c128* dA, int n, int lda, uint64_t k_begin, uint64_t k_end, perm_c128* dOut,
                      void* dWork, size_t workBytes, const perm_opts* opts, void* stream) {
+  permk::NvtxRange nvtx_range("perm_glynn_range");
   if (n < 1) return PERM_ERANGE;
   return run_fwd(dA, n, lda, permk::KIND_GLYNN, k_begin, k_end, 1, dOut, dWork, workBytes, opts, stream);
 }
 
 int perm_ryser_range(const perm_c128* dA, int n, int lda, uint64_t k_begin, uint64_t k_end, perm_c128* dOut,
                      void* dWork, size_t workBytes, const perm_opts* opts, void* stream) {
+  permk::NvtxRange nvtx_range("perm_ryser_range");
   if (n < 1) return PERM_ERANGE;
   return run_fwd(dA, n, lda, permk::KIND_RYSER, k_begin, k_end, 1, dOut, dWork, workBytes, opts, stream);
 }
@@ -370,6 +377,7 @@ size_t perm_glynn_mult_workspace_size(int n, int g, const int32_t* hMult, const 
 
 int perm_glynn_mult(const perm_c128* dB, int n, int ldb, int g, const int32_t* hMult, perm_c128* dOut, void* dWork,
                     size_t workBytes, const perm_opts* opts, void* stream) {
+  permk::NvtxRange nvtx_range("perm_glynn_mult");
   if (n < 1 || n > PERM_MAX_N) return PERM_ERANGE;
   return run_mult(dB, n, ldb, g, hMult, dOut, dWork, workBytes, opts, stream);
 }
@@ -383,6 +391,7 @@ size_t prob_sample_workspace_size(int n, const perm_opts* opts) {
 
 int prob_sample(const perm_c128* dU, int m, int ldu, const int32_t* hS, const int32_t* hT, double* hProb,
                 perm_c128* hPerm, void* dWork, size_t workBytes, const perm_opts* opts, void* stream) {
+  permk::NvtxRange nvtx_range("prob_sample");
   cudaStream_t s = (cudaStream_t)stream;
   if (m < 1 || !dU || ldu < m || !hS || !hT || !hProb || !dWork) return PERM_EINVAL;
   if (((uintptr_t)dU & 15u) || ((uintptr_t)dWork & 255u)) return PERM_EINVAL;
@@ -548,6 +557,7 @@ int noalloc_scratch(void** out) {
 
 extern "C" int perm_glynn_noalloc(const perm_c128* dA, int n, int lda, perm_c128* dOut, const perm_opts* opts,
                                   void* stream) {
+  permk::NvtxRange nvtx_range("perm_glynn_noalloc");
   if (n < 0 || n > PERM_MAX_N) return PERM_ERANGE;
   if (!dOut || (n > 0 && !dA)) return PERM_EINVAL;
   void* scratch = nullptr;

@@ -10,7 +10,7 @@
 // exceeds u_k * sum_l w_k(l).  Per step: one minors_kernel<k> launch over all
 // draws (the k minors of the (k-1) x k matrix read straight from U), then one
 // draw_kernel block per draw (minors from the block partials, weights, running
-// sums in mode order, choice).  Every launch is stream-ordered; nothing is
+// sums in mode order by a block scan, choice).  Every launch is stream-ordered; nothing is
 // copied to or from the host.
 #include <cuda_runtime.h>
 #include <limits.h>
@@ -99,7 +99,8 @@ struct DrawArgs {
   double* cum;          // [s][m] running sums
 };
 
-constexpr int DRAW_BLOCK = 256;
+constexpr int DRAW_BLOCK = 512;
+constexpr int DRAW_TILE = 2 * DRAW_BLOCK;
 
 __global__ void __launch_bounds__(DRAW_BLOCK) draw_kernel(DrawArgs a) {
   const long long s = blockIdx.x;
@@ -132,30 +133,67 @@ __global__ void __launch_bounds__(DRAW_BLOCK) draw_kernel(DrawArgs a) {
   __syncthreads();
   double* w = a.w + s * m;
   double* cum = a.cum + s * m;
-  // w(l) = |sum_j A[l, j] m_j|^2 with A[l, j] = U[in(alpha_j), l] (coalesced over l)
-  for (int l = threadIdx.x; l < m; l += blockDim.x) {
-    double ar = 0.0, ai = 0.0;
-    for (int j = 0; j < k; j++) {
-      const double2 u = a.U[(long long)s_cm[j] * a.ldu + l];
-      const double2 mm = mnr[j];
-      ar = fma(u.x, mm.x, ar);
-      ar = fma(-u.y, mm.y, ar);
-      ai = fma(u.x, mm.y, ai);
-      ai = fma(u.y, mm.x, ai);
+  // Tiles of DRAW_TILE modes (two per thread): the block computes
+  // w(l) = |sum_j A[l, j] m_j|^2, A[l, j] = U[in(alpha_j), l] (coalesced over l),
+  // then the running sums of the tile by a block-wide scan in a fixed order
+  // (thread pair sums, warp shuffles, warp totals), carried across tiles.
+  __shared__ double wt[DRAW_TILE], ct[DRAW_TILE];
+  __shared__ double wsum[DRAW_BLOCK / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double carry = 0.0;  // the same value in every thread
+  for (int l0 = 0; l0 < m; l0 += DRAW_TILE) {
+    const int len = (m - l0 < DRAW_TILE) ? m - l0 : DRAW_TILE;
+    for (int t = threadIdx.x; t < DRAW_TILE; t += blockDim.x) {
+      double wv = 0.0;
+      if (t < len) {
+        const int l = l0 + t;
+        double ar = 0.0, ai = 0.0;
+#pragma unroll 8
+        for (int j = 0; j < k; j++) {
+          const double2 u = a.U[(long long)s_cm[j] * a.ldu + l];
+          const double2 mm = mnr[j];
+          ar = fma(u.x, mm.x, ar);
+          ar = fma(-u.y, mm.y, ar);
+          ai = fma(u.x, mm.y, ai);
+          ai = fma(u.y, mm.x, ai);
+        }
+        wv = fma(ar, ar, ai * ai);
+      }
+      wt[t] = wv;
     }
-    w[l] = fma(ar, ar, ai * ai);
-  }
-  __syncthreads();
-  // running sums in mode order, one thread (a sequential sum's rounding)
-  if (threadIdx.x == 0) {
-    double c = 0.0;
-#pragma unroll 4
-    for (int l = 0; l < m; l++) {
-      c += w[l];
-      cum[l] = c;
+    __syncthreads();
+    const double a0 = wt[2 * threadIdx.x], a1 = wt[2 * threadIdx.x + 1];
+    const double pair = a0 + a1;
+    double inc = pair;  // inclusive scan of the pair sums within the warp
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const double o = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += o;
     }
-    s_W = c;
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      double v = lane < DRAW_BLOCK / 32 ? wsum[lane] : 0.0;
+#pragma unroll
+      for (int off = 1; off < DRAW_BLOCK / 32; off <<= 1) {
+        const double o = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) v += o;
+      }
+      if (lane < DRAW_BLOCK / 32) wsum[lane] = v;  // inclusive warp prefixes
+    }
+    __syncthreads();
+    const double before = carry + ((warp > 0 ? wsum[warp - 1] : 0.0) + (inc - pair));
+    ct[2 * threadIdx.x] = before + a0;
+    ct[2 * threadIdx.x + 1] = (before + a0) + a1;
+    carry = carry + wsum[DRAW_BLOCK / 32 - 1];
+    __syncthreads();
+    for (int t = threadIdx.x; t < len; t += blockDim.x) {
+      w[l0 + t] = wt[t];
+      cum[l0 + t] = ct[t];
+    }
+    __syncthreads();
   }
+  if (threadIdx.x == 0) s_W = carry;
   __syncthreads();
   const double W = s_W;
   if (!(W > 0.0) || !isfinite(W)) {
@@ -167,7 +205,7 @@ __global__ void __launch_bounds__(DRAW_BLOCK) draw_kernel(DrawArgs a) {
   const double x = a.unif[s * n + (k - 1)] * W;
   int first = INT_MAX, last = -1;
   for (int l = threadIdx.x; l < m; l += blockDim.x) {
-    if (first == INT_MAX && cum[l] > x && (l == 0 || !(cum[l - 1] > x))) first = l;
+    if (first == INT_MAX && cum[l] > x) first = l;
     if (w[l] > 0.0) last = l;
   }
   if (first != INT_MAX) atomicMin(&s_first, first);
@@ -352,6 +390,7 @@ size_t perm_row_minors_workspace_size(int k, int batch, const perm_opts* opts) {
 
 int perm_row_minors(const perm_c128* dM, int k, int ldm, int batch, int64_t strideM, perm_c128* dOut,
                     void* dWork, size_t workBytes, const perm_opts* opts, void* stream) {
+  permk::NvtxRange nvtx_range("perm_row_minors");
   cudaStream_t s = (cudaStream_t)stream;
   if (k < 1 || k > PERM_MINORS_MAX_K) return PERM_ERANGE;
   if (batch < 0) return PERM_EINVAL;
@@ -412,6 +451,7 @@ size_t boson_sample_workspace_size(int m, int n, int nsamples, const perm_opts* 
 int boson_sample(const perm_c128* dU, int m, int ldu, int n, const int32_t* hInputs, int nsamples,
                  const int32_t* dAlpha, const double* dUnif, int32_t* dR, void* dWork, size_t workBytes,
                  const perm_opts* opts, void* stream) {
+  permk::NvtxRange nvtx_range("boson_sample");
   cudaStream_t s = (cudaStream_t)stream;
   if (n < 1 || n > BOSON_SAMPLE_MAX_N) return PERM_ERANGE;
   if (m < n || ldu < m || nsamples < 0 || !hInputs) return PERM_EINVAL;

@@ -124,3 +124,12 @@ def batch_patterns(U: np.ndarray, count: int, n_lo: int, n_hi: int, seed: int, c
         cols_l.append(cols)
         collide.append(c)
     return mats, np.array(ns, dtype=np.int32), rows_l, cols_l, np.array(collide)
+
+
+def sampler_draws(n: int, count: int, seed: int) -> tuple[np.ndarray, np.ndarray]:
+    """Random inputs of ``count`` boson-sampling draws of n photons: int32 photon
+    orders (each row a uniform permutation of 0..n-1) and float64 uniforms in [0, 1)."""
+    g = rng(seed)
+    alpha = np.stack([g.permutation(n) for _ in range(count)]).astype(np.int32)
+    u = g.random((count, n))
+    return alpha, u

@@ -85,10 +85,7 @@ def test_row_minors_rank_one_full_size(pg, k):
 # --------------------------------------------------------------------------
 
 def draws(seed, nsamples, n):
-    g = np.random.default_rng(seed)
-    alpha = np.stack([g.permutation(n) for _ in range(nsamples)]).astype(np.int32)
-    u = g.random((nsamples, n))
-    return alpha, u
+    return S.sampler_draws(n, nsamples, seed)
 
 
 def check_against_oracle(U, inputs, alpha, u, got):

@@ -45,6 +45,10 @@ def ladder_errors(pg):
             for prec in ("fp64", "fp64_dd", "fp32p_dd", "fp64_df"):
                 got = val(f(dA, prec=prec))
                 errs[(method, prec)] = abs((got - want_hi) - want_lo) / abs(want_hi)
+        # R4 (double-float row sums too; Glynn only), default chunk 2^10 and 2^12
+        for name, ch in (("fp32x2", 0), ("fp32x2_c12", 12)):
+            got = val(pg.glynn(dA, prec="fp32x2", chunk_log2=ch))
+            errs[("glynn", name)] = abs((got - want_hi) - want_lo) / abs(want_hi)
         out.append((row["kind"], n, errs))
     return out
 
@@ -52,13 +56,14 @@ def ladder_errors(pg):
 def test_precision_ladder(pg):
     results = ladder_errors(pg)
     print()
-    print("%-11s %3s  %-9s %-9s %-9s %-9s | %-9s %-9s %-9s | %-9s %-9s" % (
-        "input", "n", "G fp64", "G dd", "G fp32p", "G df", "R fp64", "R dd", "R fp32p", "NW fp64", "NW dd"))
+    print("%-11s %3s  %-9s %-9s %-9s %-9s %-9s %-9s | %-9s %-9s %-9s | %-9s %-9s" % (
+        "input", "n", "G fp64", "G dd", "G fp32p", "G df", "G x2", "G x2c12", "R fp64", "R dd", "R fp32p",
+        "NW fp64", "NW dd"))
     for kind, n, e in results:
-        print("%-11s %3d  %.2e  %.2e  %.2e  %.2e  | %.2e  %.2e  %.2e  | %.2e  %.2e" % (
+        print("%-11s %3d  %.2e  %.2e  %.2e  %.2e  %.2e  %.2e  | %.2e  %.2e  %.2e  | %.2e  %.2e" % (
             kind, n, e[("glynn", "fp64")], e[("glynn", "fp64_dd")], e[("glynn", "fp32p_dd")],
-            e[("glynn", "fp64_df")], e[("ryser", "fp64")], e[("ryser", "fp64_dd")], e[("ryser", "fp32p_dd")],
-            e[("ryser_nw", "fp64")], e[("ryser_nw", "fp64_dd")]))
+            e[("glynn", "fp64_df")], e[("glynn", "fp32x2")], e[("glynn", "fp32x2_c12")], e[("ryser", "fp64")],
+            e[("ryser", "fp64_dd")], e[("ryser", "fp32p_dd")], e[("ryser_nw", "fp64")], e[("ryser_nw", "fp64_dd")]))
     for kind, n, e in results:
         # FP64 Glynn meets the 1e-10 bar on every input, with or without compensation
         assert e[("glynn", "fp64")] < REL_TOL, (kind, n)
@@ -69,6 +74,8 @@ def test_precision_ladder(pg):
         assert e[("glynn", "fp32p_dd")] < 1e-3, (kind, n)
         # double-float products keep ~48 bits: still inside the FP64 bar
         assert e[("glynn", "fp64_df")] < REL_TOL, (kind, n)
+        # double-float row sums as well (R4): ~48-bit inputs and updates, still inside the bar
+        assert e[("glynn", "fp32x2")] < REL_TOL, (kind, n)
     # the paper's finding: on cancellation-heavy input Ryser in FP64 loses many
     # more digits than BB/FG (its "special-derived" matrices; all-ones errors
     # 10^7-10^9 apart)
@@ -97,3 +104,28 @@ def test_summation_order_study_ryser_allones(pg):
         hi = max(float(p["original"]), float(p["merging"]))
         assert lo / 100 <= e_def <= hi * 100, (n, e_def)
         assert e_def < float(p["separating"]) and e_def < float(p["random"])
+
+
+def test_fp32x2_is_glynn_only(pg):
+    from paper_1606_05836_gb300 import PermError
+    A = to_dev(np.eye(6, dtype=np.complex128))
+    assert abs(val(pg.glynn(A, prec="fp32x2")) - 1.0) < 1e-14
+    with pytest.raises(PermError):
+        pg.ryser(A, prec="fp32x2")
+    with pytest.raises(PermError):
+        pg.ryser_nw(A, prec="fp32x2")
+
+
+# R3 keeps FP64 row sums and meets the FP64 bar; R4's double-float row sums carry
+# ~48 bits, and on a rank-one matrix (the Glynn terms cancel by ~10^3 relative to
+# the result at n = 32) its stated bound is 1e-9 (measured 2.9e-10).
+@pytest.mark.parametrize("prec,tol", [("fp64_df", REL_TOL), ("fp32x2", 1e-9)])
+def test_fast_rungs_rank_one_n32(pg, prec, tol):
+    """The FP32-pipe rungs at the bench's largest size against the closed form n! prod u prod v."""
+    import math
+
+    import synthetic as S
+    A, u, v = S.rank_one(32, 601)
+    want = math.factorial(32) * np.prod(u) * np.prod(v)
+    got = val(pg.glynn(to_dev(A), prec=prec))
+    assert abs(got - want) <= tol * abs(want), (prec, got, want)
