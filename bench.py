@@ -324,6 +324,18 @@ def measure_forms(dev, plain_rate):
     per8, _ = pg.batched(pick, method="glynn")
     per8 = per8.cpu().numpy()
     berr = max(ref_rel_err(r, pick[i], complex(per8[i])) for i, r in enumerate(items))
+    # the same batch in R4 (double-float walk on the FP32 pipe), same launch shape
+    bp4 = B.BatchedPermanents(mats, method="glynn", scale=scale, prec="fp32x2", unit_log2=tuned["unit_log2"],
+                              block=tuned["block"])
+    bp4.capture()
+    bp4.replay()
+    t4 = timed(bp4.replay, reps=3)
+    per8_4, _ = pg.batched(pick, method="glynn", prec="fp32x2")
+    per8_4 = per8_4.cpu().numpy()
+    berr4 = max(ref_rel_err(r, pick[i], complex(per8_4[i])) for i, r in enumerate(items))
+    forms["batched_4096_n8-24_fp32x2"] = {"terms_per_s": terms / t4, "perms_per_s": len(mats) / t4,
+                                         "s_per_replay": t4, "vs_fp64_batch": t / t4,
+                                         "max_rel_err_sampled_vs_oracle": berr4}
     forms["batched_4096_n8-24"] = {"terms_per_s": terms / t, "perms_per_s": len(mats) / t, "s_per_replay": t,
                                    "vs_plain_glynn": terms / t / base, "collision_items": int(collide.sum()),
                                    "tuned": {"unit_log2": tuned["unit_log2"], "block": tuned["block"]},
@@ -349,6 +361,9 @@ def measure_forms(dev, plain_rate):
     pg.row_minors(M32)
     tm = timed(lambda: pg.row_minors(M32))
     forms["row_minors_k32"] = {"terms_per_s": 2 ** 31 / tm, "s": tm, "cost_vs_glynn_n32": tm * base / 2 ** 31}
+    pg.row_minors(M32, prec="fp32x2")
+    tm4 = timed(lambda: pg.row_minors(M32, prec="fp32x2"))
+    forms["row_minors_k32_fp32x2"] = {"terms_per_s": 2 ** 31 / tm4, "s": tm4, "cost_vs_glynn_n32": tm4 * base / 2 ** 31}
     # boson-sampling draws: 16 draws of 24 photons in the 1000-mode unitary (one graph replay)
     m, n, ns = 1000, 24, 16
     smp, alpha, uu = sampler_case(pg, U, n, ns, 5, dev)
@@ -369,6 +384,17 @@ def measure_forms(dev, plain_rate):
                                            "cost_per_draw_in_glynn_n24": ts / ns / t24,
                                            "launches_per_replay": 2 * n - 1,
                                            "draws_equal_oracle_m30_n8": same}
+    smp4, _, _ = sampler_case(pg, U, n, ns, 5, dev, prec="fp32x2")
+    smp4.capture()
+    smp4.replay()
+    ts4 = timed(smp4.replay, reps=2)
+    s304, _, _ = sampler_case(pg, U30, 8, 4, 6, dev, prec="fp32x2")
+    got4 = s304.run().cpu().numpy()
+    same4 = "%d/4" % sum(int(list(got4[i]) == rs["draws"][i]) for i in range(4))
+    forms["boson_sample_m1000_n24_x16_fp32x2"] = {"draws_per_s": ns / ts4, "s_per_replay": ts4,
+                                                  "terms_per_s": ns * (2 ** n - 2) / ts4,
+                                                  "cost_per_draw_in_glynn_n24": ts4 / ns / t24,
+                                                  "draws_equal_oracle_m30_n8": same4}
     return forms
 
 
@@ -399,14 +425,14 @@ def ref_rel_err(ref, A, got: complex):
     return abs(d) / abs(complex(rh + rl, ih + il))
 
 
-def sampler_case(pg, U, n, ns, seed, dev):
+def sampler_case(pg, U, n, ns, seed, dev, prec="fp64"):
     """A BosonSampler on U (numpy) with photons in modes 0..n-1 and seeded draws loaded."""
     import torch
 
     import synthetic as S
 
     alpha, uu = S.sampler_draws(n, ns, seed)
-    smp = pg.BosonSampler(torch.as_tensor(U).to(dev), list(range(n)), ns)
+    smp = pg.BosonSampler(torch.as_tensor(U).to(dev), list(range(n)), ns, prec=prec)
     smp.load(torch.as_tensor(alpha).to(dev), torch.as_tensor(uu).to(dev))
     return smp, alpha, uu
 

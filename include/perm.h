@@ -68,7 +68,8 @@ typedef enum {
   PERM_FP32X2 = 4    /* R4: double-float (FP32 pair, ~48-bit) row sums updated at every step and
                         double-float products, all on the FP32 pipe; exact FP64 row sums at each
                         chunk start (default every 2^10 steps), FP64 accumulation.  Glynn only
-                        (perm_glynn, perm_glynn_range, perm_glynn_noalloc); EINVAL elsewhere */
+                        (perm_glynn, perm_glynn_range, perm_glynn_noalloc, perm_batched with
+                        method 0, perm_row_minors, boson_sample); EINVAL elsewhere */
 } perm_prec;
 
 /* Launch options; pass NULL for the defaults (every field 0 = default). */
@@ -125,7 +126,8 @@ int perm_ryser_range(const perm_c128* dA, int n, int lda, uint64_t k_begin, uint
  * dPacked:  all matrices, row-major, item i at dPacked + dOffsets[i] with lda = n_i.
  * dOffsets: int64 offsets in complex elements (device), dN: int32 sizes (device);
  * hN:       the same sizes on the host (used only to size the workspace layout).
- * method:   0 = Glynn (Eq. (S2)), 1 = Ryser (Eq. (S1)).
+ * method:   0 = Glynn (Eq. (S2)), 1 = Ryser (Eq. (S1)); opts->prec R0-R3 for both,
+ *           PERM_FP32X2 (R4) for Glynn only.
  * dScale:   nullable per-item factor for the probability, e.g. 1/(prod s_i! prod t_j!).
  * dOut:     per-item Per (perm_c128).  dProb: nullable per-item |Per|^2 * scale.
  * dWork:    256-byte-aligned workspace of perm_batched_workspace_size() bytes.
@@ -232,7 +234,8 @@ int perm_glynn_noalloc(const perm_c128* dA, int n, int lda, perm_c128* dOut, con
  * Gray-code pass per matrix: appending a free last row x to M, Supp. Eq. (S2)
  * of arXiv 1606.05836 is linear in x and m_j is the coefficient of x_j,
  *     m_j = 2^-(k-1) sum_delta (prod delta) delta_j prod_{i<k-1} (sum_l delta_l M_il).
- * (The paper has no such routine; the boson sampler below needs it.)  Plain FP64.
+ * (The paper has no such routine; the boson sampler below needs it.)  opts->prec
+ * PERM_FP64 (default) or PERM_FP32X2 (the walk in double-float, as for perm_glynn).
  *
  * dM:    batch matrices (device, complex128, row-major, k-1 rows of k entries,
  *        row stride ldm >= k); matrix b at dM + b*strideM elements.
@@ -269,6 +272,7 @@ int perm_row_minors(const perm_c128* dM, int k, int ldm, int batch, int64_t stri
  *           has all n entries -1.
  * dWork:    256-byte-aligned, boson_sample_workspace_size(m, n, nsamples) bytes
  *           (O(nsamples x (16 m + 8 n) + partials)).
+ * opts->prec PERM_FP64 (default) or PERM_FP32X2 selects the row minors' arithmetic.
  * 1 <= n <= BOSON_SAMPLE_MAX_N, n <= m.  2n - 1 kernel launches, all on
  * `stream`, no host synchronisation (the call may be captured in a CUDA graph
  * once the workspace exists). */

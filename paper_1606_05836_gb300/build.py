@@ -29,9 +29,9 @@ NVFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I",
 # template instances build in parallel).
 MULTI = {
     "fwd_inst.cu": ["-DPERM_PART=%d" % p for p in range(8)],
-    "batched_inst.cu": ["-DPERM_PREC=%d" % p for p in range(4)],
+    "batched_inst.cu": ["-DPERM_PREC=%d" % p for p in range(5)],
     "grad_inst.cu": ["-DPERM_PART=%d" % p for p in range(4)],
-    "minors_inst.cu": ["-DPERM_PART=%d" % p for p in range(2)],
+    "minors_inst.cu": ["-DPERM_PART=%d" % p for p in range(4)],
 }
 
 

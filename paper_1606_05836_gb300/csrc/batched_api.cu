@@ -123,7 +123,16 @@ __global__ void __launch_bounds__(128) batch_prep_kernel(BatchArgs a) {
       const double f = pow2_double(s_row[i]);
       const double2 v = A[i * n + j];
       C[j * n + i] = make_double2(v.x * f, v.y * f);
-      if (a.kind == KIND_GLYNN && j >= 1) C[n * n + (j - 1) * n + i] = make_double2(2.0 * v.x * f, 2.0 * v.y * f);
+      if (a.kind == KIND_GLYNN && j >= 1) {
+        const double sr = 2.0 * v.x * f, si = 2.0 * v.y * f;
+        if (a.prec == PERM_FP32X2) {
+          // R4 walks add the step columns in double-float (16 bytes, same slot)
+          const df re = f64_to_df(sr), im = f64_to_df(si);
+          reinterpret_cast<float4*>(C)[n * n + (j - 1) * n + i] = make_float4(re.h, re.l, im.h, im.l);
+        } else {
+          C[n * n + (j - 1) * n + i] = make_double2(sr, si);
+        }
+      }
     }
     if (threadIdx.x == 0) {
       int sum = 0;
@@ -189,11 +198,11 @@ struct Layout {
 
 int batch_opts(const perm_opts* o, int* prec, int* chunk, int* unit, int* block, int* grid) {
   *prec = o ? o->prec : PERM_FP64;
-  *chunk = (o && o->chunk_log2) ? o->chunk_log2 : 12;
+  *chunk = (o && o->chunk_log2) ? o->chunk_log2 : ((o && o->prec == PERM_FP32X2) ? 10 : 12);
   *unit = (o && o->unit_log2) ? o->unit_log2 : 11;
   *block = (o && o->block) ? o->block : 128;
   *grid = o ? o->grid : 0;
-  if (*prec < PERM_FP64 || *prec > PERM_FP64_DF) return PERM_EINVAL;
+  if (*prec < PERM_FP64 || *prec > PERM_FP32X2) return PERM_EINVAL;
   if (*chunk < 1 || *chunk > 30 || *unit < 0 || *unit > 30) return PERM_EINVAL;
   if (*block < 32 || *block > 256 || (*block & 31) || *grid < 0) return PERM_EINVAL;
   return PERM_OK;
@@ -229,6 +238,7 @@ int walk_launch(int prec, const BatchArgs& a, int grid, int block, cudaStream_t 
   if (prec == 1) return launch_batch_walk<1>(a, grid, block, s);
   if (prec == 2) return launch_batch_walk<2>(a, grid, block, s);
   if (prec == 3) return launch_batch_walk<3>(a, grid, block, s);
+  if (prec == 4) return launch_batch_walk<4>(a, grid, block, s);
   return launch_batch_walk<0>(a, grid, block, s);
 }
 
@@ -236,6 +246,7 @@ int walk_occupancy(int prec, int block, int* out) {
   if (prec == 1) return batch_walk_blocks_per_sm<1>(block, out);
   if (prec == 2) return batch_walk_blocks_per_sm<2>(block, out);
   if (prec == 3) return batch_walk_blocks_per_sm<3>(block, out);
+  if (prec == 4) return batch_walk_blocks_per_sm<4>(block, out);
   return batch_walk_blocks_per_sm<0>(block, out);
 }
 
@@ -247,6 +258,7 @@ size_t perm_batched_workspace_size(int count, const int32_t* hN, int method, con
   int prec, chunk, unit, block, grid;
   if (count < 0 || (count > 0 && !hN) || (method != 0 && method != 1)) return 0;
   if (batch_opts(opts, &prec, &chunk, &unit, &block, &grid)) return 0;
+  if (prec == PERM_FP32X2 && method != 0) return 0;  // R4 is a Glynn walk
   Layout L;
   if (make_layout(count, hN, method == 0 ? KIND_GLYNN : KIND_RYSER, unit, &L)) return 0;
   return L.total;
@@ -264,6 +276,7 @@ int perm_batched(const perm_c128* dPacked, const int64_t* dOffsets, const int32_
   int prec, chunk, unit, block, grid;
   int st = batch_opts(opts, &prec, &chunk, &unit, &block, &grid);
   if (st) return st;
+  if (prec == PERM_FP32X2 && method != 0) return PERM_EINVAL;  // R4 is a Glynn walk
   const int kind = method == 0 ? KIND_GLYNN : KIND_RYSER;
   Layout L;
   st = make_layout(count, hN, kind, unit, &L);
@@ -276,6 +289,7 @@ int perm_batched(const perm_c128* dPacked, const int64_t* dOffsets, const int32_
   a.ns = (const int*)dN;
   a.count = count;
   a.kind = kind;
+  a.prec = prec;
   a.unit_log2 = unit;
   a.chunk_log2 = chunk;
   a.neg_zero = -0.0;

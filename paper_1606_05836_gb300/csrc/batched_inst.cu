@@ -1,9 +1,9 @@
 // Instantiation of the persistent batched walk kernel for one precision rung
-// (compiled once per rung with -DPERM_PREC=0,1,2 so the three build in parallel).
+// (compiled once per rung with -DPERM_PREC=0..4 so the rungs build in parallel).
 #include "batched_kernel.cuh"
 
 #ifndef PERM_PREC
-#error "compile with -DPERM_PREC=<0..2>"
+#error "compile with -DPERM_PREC=<0..4>"
 #endif
 
 namespace permk {

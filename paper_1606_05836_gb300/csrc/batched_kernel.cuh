@@ -52,6 +52,7 @@ struct BatchArgs {
   const int* ns;
   int count;
   int kind;
+  int prec;                // R4: the doubled step columns are stored as double-float
   int unit_log2;
   int chunk_log2;
   double neg_zero;
@@ -81,10 +82,14 @@ __device__ __forceinline__ void batch_walk_n(int n, const double2* Acol, const d
                                              uint64_t ke, uint64_t CH, double nz, double& ar, double& ai, double& cr,
                                              double& ci) {
   switch (n) {
-#define PERM_BCASE(N)                                                                              \
-  case N:                                                                                          \
-    walk_range<N, PREC, TUNE, true>(Acol, Step, nullptr, nullptr, nullptr, nullptr, N,                     \
-                                    glynn ? KIND_GLYNN : KIND_RYSER, kb, ke, CH, nz, ar, ai, cr, ci);         \
+#define PERM_BCASE(N)                                                                                      \
+  case N:                                                                                                  \
+    if constexpr (PREC == 4) {                                                                             \
+      walk_range_df<N>(Acol, reinterpret_cast<const float4*>(Step), N, kb, ke, CH, ar, ai);                \
+    } else {                                                                                               \
+      walk_range<N, PREC, TUNE, true>(Acol, Step, nullptr, nullptr, nullptr, nullptr, N,                   \
+                                      glynn ? KIND_GLYNN : KIND_RYSER, kb, ke, CH, nz, ar, ai, cr, ci);     \
+    }                                                                                                      \
     break;
     PERM_BCASE(1) PERM_BCASE(2) PERM_BCASE(3) PERM_BCASE(4) PERM_BCASE(5) PERM_BCASE(6) PERM_BCASE(7)
     PERM_BCASE(8) PERM_BCASE(9) PERM_BCASE(10) PERM_BCASE(11) PERM_BCASE(12) PERM_BCASE(13) PERM_BCASE(14)

@@ -282,6 +282,30 @@ __device__ __forceinline__ df df_add(const df a, const df b) {
   return df{h, __fsub_rn(t, __fsub_rn(h, s))};
 }
 
+// prod_i v_i of double-float values as two interleaved chains (even and odd
+// rows, then one multiply joining them): the same n - 1 multiplies with twice the
+// independent work in flight, which the few warps per SM sub-partition need.
+// Above 28 factors the second chain's registers would spill: one chain there.
+template <int N>
+__device__ __forceinline__ void prod_df2(const float (&rh)[N], const float (&rl)[N], const float (&ih)[N],
+                                         const float (&il)[N], df& pr, df& pi) {
+  pr = df{rh[0], rl[0]};
+  pi = df{ih[0], il[0]};
+  if constexpr (N > 28) {
+#pragma unroll
+    for (int i = 1; i < N; i++) dfc_mul(pr, pi, df{rh[i], rl[i]}, df{ih[i], il[i]});
+  } else if constexpr (N > 1) {
+    df qr{rh[1], rl[1]}, qi{ih[1], il[1]};
+#pragma unroll
+    for (int i = 2; i + 1 < N; i += 2) {
+      dfc_mul(pr, pi, df{rh[i], rl[i]}, df{ih[i], il[i]});
+      dfc_mul(qr, qi, df{rh[i + 1], rl[i + 1]}, df{ih[i + 1], il[i + 1]});
+    }
+    if constexpr (N % 2 == 1) dfc_mul(pr, pi, df{rh[N - 1], rl[N - 1]}, df{ih[N - 1], il[N - 1]});
+    dfc_mul(pr, pi, qr, qi);
+  }
+}
+
 // Glynn walk over [kb, ke) with double-float row sums: exact FP64 row sums at
 // every chunk start (from Acol), split into double-float; each step adds or
 // subtracts the flipped doubled column (StepF, double-float (re h, re l, im h,
@@ -324,9 +348,8 @@ __device__ __forceinline__ void walk_range_df(const double2* __restrict__ Acol, 
     uint64_t k = c0;
 #pragma unroll 1
     while (true) {
-      df pr{rh[0], rl[0]}, pi{ih[0], il[0]};
-#pragma unroll
-      for (int i = 1; i < N; i++) dfc_mul(pr, pi, df{rh[i], rl[i]}, df{ih[i], il[i]});
+      df pr, pi;
+      prod_df2<N>(rh, rl, ih, il, pr, pi);
       const double xr = f32_to_f64_int(pr.h) + f32_to_f64_int(pr.l);
       const double xi = f32_to_f64_int(pi.h) + f32_to_f64_int(pi.l);
       const unsigned long long smask = (k & 1ull) << 63;  // (prod delta) = (-1)^(k & 1)

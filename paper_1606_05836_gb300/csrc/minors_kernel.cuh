@@ -44,7 +44,87 @@ struct MinorsArgs {
 
 __device__ __forceinline__ int clamp_index(int x, int lim) { return (x >= 0 && x < lim) ? x : 0; }
 
+// R4 (PREC = 4): double-float row sums and products on the FP32 pipe (as the
+// forward kernel's R4), the doubled columns rounded to double-float in shared
+// memory and the row sums re-split from FP64 sums of those same columns at every
+// chunk start; S and H stay FP64.
 template <int K>
+__device__ __forceinline__ void minors_walk_df(const double2* Col0, const float4* StepF, double2* Hs, uint64_t kb,
+                                               uint64_t ke, uint64_t CH, double& sr, double& si) {
+  constexpr int R = K - 1;
+  constexpr int NP = Stride<R>::value;
+  constexpr int B = MINORS_BLOCK;
+  uint64_t k = kb;
+  uint64_t g = kb ^ (kb >> 1);
+  while (k < ke) {
+    const uint64_t c1 = (ke - k > CH) ? k + CH : ke;
+    float rh[R], rl[R], ih[R], il[R];
+    {
+      double vr[R], vi[R];
+#pragma unroll
+      for (int i = 0; i < R; i++) {
+        const double2 x = Col0[i];
+        vr[i] = x.x + x.x;
+        vi[i] = x.y + x.y;
+      }
+#pragma unroll 1
+      for (int b = 0; b < K - 1; b++) {
+        const double coef = ((g >> b) & 1ull) ? -1.0 : 1.0;
+        const float4* col = StepF + b * NP;
+#pragma unroll
+        for (int i = 0; i < R; i++) {
+          const float4 x = col[i];
+          vr[i] = fma(coef, f32_to_f64_int(x.x) + f32_to_f64_int(x.y), vr[i]);
+          vi[i] = fma(coef, f32_to_f64_int(x.z) + f32_to_f64_int(x.w), vi[i]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < R; i++) {
+        const df u = f64_to_df(0.5 * vr[i]), v = f64_to_df(0.5 * vi[i]);
+        rh[i] = u.h;
+        rl[i] = u.l;
+        ih[i] = v.h;
+        il[i] = v.l;
+      }
+    }
+#pragma unroll 1
+    while (true) {
+      df pr, pi;
+      prod_df2<R>(rh, rl, ih, il, pr, pi);
+      const double xr = f32_to_f64_int(pr.h) + f32_to_f64_int(pr.l);
+      const double xi = f32_to_f64_int(pi.h) + f32_to_f64_int(pi.l);
+      const unsigned long long smask = (k & 1ull) << 63;  // prod delta = (-1)^(k & 1)
+      sr += xor_sign(xr, smask);
+      si += xor_sign(xi, smask);
+      ++k;
+      if (k >= ke) break;
+      const int b = __ffsll((long long)k) - 1;
+      {
+        const double f = xor_sign(2.0, ((g >> b) & 1ull) << 63);
+        double2 h = Hs[(b + 1) * B];
+        h.x = fma(f, sr, h.x);
+        h.y = fma(f, si, h.y);
+        Hs[(b + 1) * B] = h;
+      }
+      g ^= 1ull << b;
+      if (k >= c1) break;
+      const float sg = ((g >> b) & 1ull) ? -1.0f : 1.0f;
+      const float4* col = StepF + b * NP;
+#pragma unroll
+      for (int i = 0; i < R; i++) {
+        const float4 x = col[i];
+        const df u = df_add(df{rh[i], rl[i]}, df{__fmul_rn(sg, x.x), __fmul_rn(sg, x.y)});
+        const df v = df_add(df{ih[i], il[i]}, df{__fmul_rn(sg, x.z), __fmul_rn(sg, x.w)});
+        rh[i] = u.h;
+        rl[i] = u.l;
+        ih[i] = v.h;
+        il[i] = v.l;
+      }
+    }
+  }
+}
+
+template <int K, int PREC>
 __global__ void __launch_bounds__(MINORS_BLOCK, 2) minors_kernel(MinorsArgs a) {
   constexpr int R = K - 1;                      // rows in the product
   constexpr int NP = Stride<(R > 0 ? R : 1)>::value;
@@ -109,6 +189,20 @@ __global__ void __launch_bounds__(MINORS_BLOCK, 2) minors_kernel(MinorsArgs a) {
   double sr = 0.0, si = 0.0;  // S
   uint64_t k = kb;
   uint64_t g = kb ^ (kb >> 1);
+  if constexpr (PREC == 4 && R >= 2) {
+    // the doubled columns to double-float, in place (16 bytes each)
+    float4* StepF = reinterpret_cast<float4*>(Step);
+    for (int idx = threadIdx.x; idx < (K - 1) * R; idx += B) {
+      const int b = idx / R, i = idx % R;
+      const double2 v = Step[b * NP + i];
+      const df re = f64_to_df(v.x), im = f64_to_df(v.y);
+      StepF[b * NP + i] = make_float4(re.h, re.l, im.h, im.l);
+    }
+    __syncthreads();
+    minors_walk_df<K>(Col0, StepF, Hs, kb, ke, CH, sr, si);
+    k = ke;
+    g = (ke > kb) ? ((ke - 1) ^ ((ke - 1) >> 1)) : g;  // the last term's signs
+  } else {
   while (k < ke) {
     const uint64_t c1 = (ke - k > CH) ? k + CH : ke;
     double vr[R > 0 ? R : 1], vi[R > 0 ? R : 1];
@@ -170,6 +264,7 @@ __global__ void __launch_bounds__(MINORS_BLOCK, 2) minors_kernel(MinorsArgs a) {
       }
     }
   }
+  }
   // G_j = H_j + delta_j S (delta_0 = +1, H_0 = 0)
   Hs[0] = make_double2(sr, si);
   for (int j = 1; j < K; j++) {
@@ -210,8 +305,8 @@ inline size_t minors_smem_bytes(int K) {
 }
 
 template <int K>
-int launch_minors(const MinorsArgs& a, int grid, cudaStream_t s);
+int launch_minors(const MinorsArgs& a, int prec, int grid, cudaStream_t s);
 template <int K>
-int minors_blocks_per_sm(int* out);
+int minors_blocks_per_sm(int prec, int* out);
 
 }  // namespace permk

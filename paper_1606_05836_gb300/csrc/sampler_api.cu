@@ -233,11 +233,11 @@ int sfail(int e) {
   X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) X(17) X(18) X(19) X(20) \
   X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30) X(31) X(32)
 
-int dispatch_minors(int k, const MinorsArgs& a, int grid, cudaStream_t s) {
+int dispatch_minors(int k, const MinorsArgs& a, int prec, int grid, cudaStream_t s) {
   switch (k) {
 #define PERM_MC(K) \
   case K:          \
-    return launch_minors<K>(a, grid, s);
+    return launch_minors<K>(a, prec, grid, s);
     PERM_M_CASES(PERM_MC)
 #undef PERM_MC
     default:
@@ -245,11 +245,11 @@ int dispatch_minors(int k, const MinorsArgs& a, int grid, cudaStream_t s) {
   }
 }
 
-int dispatch_minors_occupancy(int k, int* out) {
+int dispatch_minors_occupancy(int k, int prec, int* out) {
   switch (k) {
 #define PERM_MC(K) \
   case K:          \
-    return minors_blocks_per_sm<K>(out);
+    return minors_blocks_per_sm<K>(prec, out);
     PERM_M_CASES(PERM_MC)
 #undef PERM_MC
     default:
@@ -260,10 +260,11 @@ int dispatch_minors_occupancy(int k, int* out) {
 // Resident blocks per SM of minors_kernel<k>, cached per device.
 constexpr int MAX_DEVICES = 64;
 std::mutex g_occ_mu;
-int g_occ[MAX_DEVICES][MINORS_MAX_K + 1];
+int g_occ[MAX_DEVICES][2][MINORS_MAX_K + 1];
 int g_sms[MAX_DEVICES];
 
-int minors_wave(int k, long long* wave) {
+int minors_wave(int k, int prec, long long* wave) {
+  const int pi = prec == PERM_FP32X2 ? 1 : 0;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return sfail((int)e);
@@ -275,26 +276,28 @@ int minors_wave(int k, long long* wave) {
     if (e != cudaSuccess) return sfail((int)e);
     g_sms[dev] = sms;
   }
-  if (g_occ[dev][k] == 0) {
+  if (g_occ[dev][pi][k] == 0) {
     int bps = 0;
-    const int oe = dispatch_minors_occupancy(k, &bps);
+    const int oe = dispatch_minors_occupancy(k, prec, &bps);
     if (oe) return sfail(oe);
     if (bps < 1) return sfail((int)cudaErrorInvalidConfiguration);
-    g_occ[dev][k] = bps;
+    g_occ[dev][pi][k] = bps;
   }
-  *wave = (long long)g_sms[dev] * g_occ[dev][k];
+  *wave = (long long)g_sms[dev] * g_occ[dev][pi][k];
   return PERM_OK;
 }
 
 struct MinorsPlan {
-  int bpi, chunk_log2;
+  int bpi, chunk_log2, prec;
   uint64_t per_q, per_r;
 };
 
-int read_minors_opts(const perm_opts* o, int* chunk, int* grid) {
-  if (o && o->prec != PERM_FP64) return PERM_EINVAL;
+// FP64 (R0) or R4; R4's default chunk is 2^10 as in the forward kernel
+int read_minors_opts(const perm_opts* o, int* prec, int* chunk, int* grid) {
+  *prec = o ? o->prec : PERM_FP64;
+  if (*prec != PERM_FP64 && *prec != PERM_FP32X2) return PERM_EINVAL;
   if (o && o->block != 0 && o->block != MINORS_BLOCK) return PERM_EINVAL;
-  *chunk = (o && o->chunk_log2) ? o->chunk_log2 : 12;
+  *chunk = (o && o->chunk_log2) ? o->chunk_log2 : (*prec == PERM_FP32X2 ? 10 : 12);
   if (*chunk < 1 || *chunk > 30) return PERM_EINVAL;
   *grid = o ? o->grid : 0;
   if (*grid < 0) return PERM_EINVAL;
@@ -304,8 +307,8 @@ int read_minors_opts(const perm_opts* o, int* chunk, int* grid) {
 // Blocks per item: enough lanes for >= 64 Gray indices each, and no more than a
 // resident wave shared by all items (opts->grid, when set, fixes it).
 int plan_minors(int k, long long items, const perm_opts* o, MinorsPlan* p) {
-  int chunk, grid;
-  int st = read_minors_opts(o, &chunk, &grid);
+  int prec, chunk, grid;
+  int st = read_minors_opts(o, &prec, &chunk, &grid);
   if (st) return st;
   const uint64_t T = 1ull << (k - 1);
   long long bpi;
@@ -313,7 +316,7 @@ int plan_minors(int k, long long items, const perm_opts* o, MinorsPlan* p) {
     bpi = grid;
   } else {
     long long wave = 0;
-    st = minors_wave(k, &wave);
+    st = minors_wave(k, prec, &wave);
     if (st) return st;
     const long long by_work = (long long)((T + 64ull * MINORS_BLOCK - 1) / (64ull * MINORS_BLOCK));
     const long long by_wave = (wave + items - 1) / items;
@@ -323,6 +326,7 @@ int plan_minors(int k, long long items, const perm_opts* o, MinorsPlan* p) {
   if (items * bpi > INT_MAX) return PERM_EINVAL;
   p->bpi = (int)bpi;
   p->chunk_log2 = chunk;
+  p->prec = prec;
   const uint64_t lanes = (uint64_t)bpi * MINORS_BLOCK;
   p->per_q = T / lanes;
   p->per_r = T % lanes;
@@ -427,7 +431,7 @@ int perm_row_minors(const perm_c128* dM, int k, int ldm, int batch, int64_t stri
   a.neg_zero = -0.0;
   a.partials = (double*)(w + L.partials);
   a.scale_exp = (int*)(w + L.scale_exp);
-  int le = dispatch_minors(k, a, batch * L.plan.bpi, s);
+  int le = dispatch_minors(k, a, L.plan.prec, batch * L.plan.bpi, s);
   if (le) return sfail(le);
   MinorsReduceArgs r;
   r.partials = a.partials;
@@ -487,7 +491,7 @@ int boson_sample(const perm_c128* dU, int m, int ldu, int n, const int32_t* hInp
   if (e != cudaSuccess) return sfail((int)e);
 
   for (int k = 1; k <= n; k++) {
-    MinorsPlan p{1, 12, 0, 0};
+    MinorsPlan p{1, 12, 0, 0, 0};
     if (k >= 2) {
       st = plan_minors(k, nsamples, opts, &p);
       if (st) return st;
@@ -509,7 +513,7 @@ int boson_sample(const perm_c128* dU, int m, int ldu, int n, const int32_t* hInp
       a.neg_zero = -0.0;
       a.partials = (double*)(w + L.partials);
       a.scale_exp = nullptr;
-      int le = dispatch_minors(k, a, nsamples * p.bpi, s);
+      int le = dispatch_minors(k, a, p.prec, nsamples * p.bpi, s);
       if (le) return sfail(le);
     }
     DrawArgs d;

@@ -20,7 +20,7 @@ import ctypes
 import torch
 
 from . import _native
-from ._native import Opts
+from ._native import PRECISIONS, Opts
 
 PERM_MINORS_MAX_K = 32
 BOSON_SAMPLE_MAX_N = 32
@@ -41,11 +41,18 @@ def _stream(dev):
     return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
 
 
-def row_minors(M: torch.Tensor, chunk_log2: int = 0, grid: int = 0) -> torch.Tensor:
+def _prec(prec) -> int:
+    if prec not in ("fp64", "fp32x2"):
+        raise ValueError("row minors and draws support prec 'fp64' or 'fp32x2'")
+    return PRECISIONS[prec]
+
+
+def row_minors(M: torch.Tensor, prec: str = "fp64", chunk_log2: int = 0, grid: int = 0) -> torch.Tensor:
     """m_j = Per(M without column j) for M of shape (k-1, k) or (batch, k-1, k).
 
-    Returns complex128 of shape (k,) or (batch, k).  ``grid`` > 0 fixes the
-    blocks per matrix.
+    Returns complex128 of shape (k,) or (batch, k).  ``prec`` "fp32x2" runs the
+    walk in double-float on the FP32 pipe (R4).  ``grid`` > 0 fixes the blocks
+    per matrix.
     """
     lib = _native.load()
     if not isinstance(M, torch.Tensor) or not M.is_cuda or M.dtype != torch.complex128:
@@ -60,7 +67,7 @@ def row_minors(M: torch.Tensor, chunk_log2: int = 0, grid: int = 0) -> torch.Ten
     if k > PERM_MINORS_MAX_K:
         raise ValueError("row_minors supports k <= %d" % PERM_MINORS_MAX_K)
     dev = M.device
-    o = Opts(0, int(chunk_log2), 0, int(grid), 0)
+    o = Opts(_prec(prec), int(chunk_log2), 0, int(grid), 0)
     out = torch.empty(batch, k, dtype=torch.complex128, device=dev)
     with torch.cuda.device(dev):
         nbytes = int(lib.perm_row_minors_workspace_size(k, batch, ctypes.byref(o)))
@@ -82,9 +89,12 @@ class BosonSampler:
     permutation of 0..n-1) and float64 (nsamples, n) uniforms in [0, 1), both on
     U's device, and returns the int32 (nsamples, n) drawn output modes (draw
     order; -1 for a draw with invalid inputs or a step of zero total weight).
+    ``prec`` "fp32x2" computes the row minors in double-float (R4, ~4x faster;
+    weights to ~1e-12, which can change a draw only at a near-tie).
     """
 
-    def __init__(self, U: torch.Tensor, inputs, nsamples: int, chunk_log2: int = 0, grid: int = 0):
+    def __init__(self, U: torch.Tensor, inputs, nsamples: int, prec: str = "fp64", chunk_log2: int = 0,
+                 grid: int = 0):
         self.lib = _native.load()
         if not isinstance(U, torch.Tensor) or not U.is_cuda or U.dtype != torch.complex128:
             raise TypeError("U must be a complex128 CUDA tensor")
@@ -98,7 +108,7 @@ class BosonSampler:
             raise ValueError("1 <= n <= %d photons" % BOSON_SAMPLE_MAX_N)
         self.nsamples = int(nsamples)
         self.device = U.device
-        self.opts = Opts(0, int(chunk_log2), 0, int(grid), 0)
+        self.opts = Opts(_prec(prec), int(chunk_log2), 0, int(grid), 0)
         self.h_inputs = (ctypes.c_int32 * self.n)(*self.inputs)
         with torch.cuda.device(self.device):
             nbytes = int(self.lib.boson_sample_workspace_size(self.m, self.n, self.nsamples, ctypes.byref(self.opts)))
@@ -152,8 +162,8 @@ class BosonSampler:
         return self.out
 
 
-def boson_sample(U: torch.Tensor, inputs, alpha: torch.Tensor, unif: torch.Tensor, chunk_log2: int = 0,
-                 grid: int = 0) -> torch.Tensor:
+def boson_sample(U: torch.Tensor, inputs, alpha: torch.Tensor, unif: torch.Tensor, prec: str = "fp64",
+                 chunk_log2: int = 0, grid: int = 0) -> torch.Tensor:
     """One batch of draws (see ``BosonSampler``)."""
-    S = BosonSampler(U, inputs, int(alpha.shape[0]), chunk_log2=chunk_log2, grid=grid)
+    S = BosonSampler(U, inputs, int(alpha.shape[0]), prec=prec, chunk_log2=chunk_log2, grid=grid)
     return S.run(alpha.to(U.device, torch.int32), unif.to(U.device, torch.float64)).clone()

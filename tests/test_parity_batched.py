@@ -31,12 +31,25 @@ def _mixed(count, n_lo, n_hi, seed):
 def test_batched_small_mixed_all_rungs(pg, method):
     mats = _mixed(48, 1, 14, 1)
     want = [oracle.perm_def(A) if A.shape[0] <= 8 else oracle.ryser(A) for A in mats]
-    tol = {"fp64": REL_TOL, "fp64_dd": REL_TOL, "fp32p_dd": 1e-4 if method == "glynn" else 1e-2, "fp64_df": REL_TOL}
-    for prec in ("fp64", "fp64_dd", "fp32p_dd", "fp64_df"):
+    tol = {"fp64": REL_TOL, "fp64_dd": REL_TOL, "fp32p_dd": 1e-4 if method == "glynn" else 1e-2, "fp64_df": REL_TOL,
+           "fp32x2": REL_TOL}
+    rungs = ("fp64", "fp64_dd", "fp32p_dd", "fp64_df") + (("fp32x2",) if method == "glynn" else ())
+    for prec in rungs:
         per, _ = pg.batched(mats, method=method, prec=prec)
         got = per.cpu().numpy()
         for i, w in enumerate(want):
             assert w.rel_err(got[i]) < tol[prec], (prec, i, mats[i].shape[0], got[i], w.hi)
+
+
+def test_batched_fp32x2_larger_items_and_ryser_rejected(pg):
+    """R4 on items up to n = 22 with several units per item, against the oracle; Ryser refuses R4."""
+    mats = _mixed(12, 16, 22, 5)
+    per, _ = pg.batched(mats, method="glynn", prec="fp32x2", unit_log2=6)
+    got = per.cpu().numpy()
+    for i, A in enumerate(mats):
+        assert oracle.ryser(A).rel_err(got[i]) < REL_TOL, (i, A.shape[0])
+    with pytest.raises(Exception):
+        pg.batched(mats[:2], method="ryser", prec="fp32x2")
 
 
 def test_batched_matches_single_permanent_path(pg):
