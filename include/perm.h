@@ -65,7 +65,8 @@ typedef enum {
   PERM_FP32P_DD = 2, /* R2: FP32 n-way products of the FP64 row sums, double-double accumulation */
   PERM_FP64_DF = 3,  /* R3: the FP64 row sums split into FP32 pairs (~48 bits) and multiplied in
                         double-float arithmetic on the FP32 pipe, FP64 accumulation */
-  PERM_FP32X2 = 4    /* R4: double-float (FP32 pair, ~48-bit) row sums updated at every step and
+  PERM_FP32X2 = 4    /* R4 (opt-in; relaxes the FP64 row-sum updates the rungs above keep):
+                        double-float (FP32 pair, ~48-bit) row sums updated at every step and
                         double-float products, all on the FP32 pipe; exact FP64 row sums at each
                         chunk start (default every 2^10 steps), FP64 accumulation.  Glynn only
                         (perm_glynn, perm_glynn_range, perm_glynn_noalloc, perm_batched with

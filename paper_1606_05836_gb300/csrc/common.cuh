@@ -271,39 +271,28 @@ __device__ __forceinline__ void prod_df(const double (&vr)[N], const double (&vi
 }
 
 // R4: double-float row sums as well, so the whole walk runs on the FP32 pipe.
-// Two-sum of the high parts, low parts added, renormalised (Dekker's double-
-// length addition); the _rn intrinsics keep it from being contracted.
-__device__ __forceinline__ df df_add(const df a, const df b) {
-  const float s = __fadd_rn(a.h, b.h);
-  const float bb = __fsub_rn(s, a.h);
-  const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
-  const float t = __fadd_rn(e, __fadd_rn(a.l, b.l));
-  const float h = __fadd_rn(s, t);
-  return df{h, __fsub_rn(t, __fsub_rn(h, s))};
-}
 
-// prod_i v_i of double-float values as two interleaved chains (even and odd
-// rows, then one multiply joining them): the same n - 1 multiplies with twice the
-// independent work in flight, which the few warps per SM sub-partition need.
-// Above 28 factors the second chain's registers would spill: one chain there.
+// prod_i v_i of double-float values (one chain of n - 1 multiplies).
 template <int N>
-__device__ __forceinline__ void prod_df2(const float (&rh)[N], const float (&rl)[N], const float (&ih)[N],
+__device__ __forceinline__ void prod_dfv(const float (&rh)[N], const float (&rl)[N], const float (&ih)[N],
                                          const float (&il)[N], df& pr, df& pi) {
   pr = df{rh[0], rl[0]};
   pi = df{ih[0], il[0]};
-  if constexpr (N > 28) {
 #pragma unroll
-    for (int i = 1; i < N; i++) dfc_mul(pr, pi, df{rh[i], rl[i]}, df{ih[i], il[i]});
-  } else if constexpr (N > 1) {
-    df qr{rh[1], rl[1]}, qi{ih[1], il[1]};
-#pragma unroll
-    for (int i = 2; i + 1 < N; i += 2) {
-      dfc_mul(pr, pi, df{rh[i], rl[i]}, df{ih[i], il[i]});
-      dfc_mul(qr, qi, df{rh[i + 1], rl[i + 1]}, df{ih[i + 1], il[i + 1]});
-    }
-    if constexpr (N % 2 == 1) dfc_mul(pr, pi, df{rh[N - 1], rl[N - 1]}, df{ih[N - 1], il[N - 1]});
-    dfc_mul(pr, pi, qr, qi);
-  }
+  for (int i = 1; i < N; i++) dfc_mul(pr, pi, df{rh[i], rl[i]}, df{ih[i], il[i]});
+}
+
+// a + sg * b in double-float for sg = +-1: Dekker's double-length addition (two-
+// sum of the high parts, low parts added, renormalised) with the sign folded into
+// the FMAs (sg * b is exact, so each FMA rounds exactly as the plain sum would);
+// the _rn intrinsics keep the error-free steps from being contracted.
+__device__ __forceinline__ df df_add_signed(const df a, const df b, float sg) {
+  const float s = __fmaf_rn(sg, b.h, a.h);
+  const float bb = __fsub_rn(s, a.h);
+  const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fmaf_rn(sg, b.h, -bb));
+  const float t = __fadd_rn(e, __fmaf_rn(sg, b.l, a.l));
+  const float h = __fadd_rn(s, t);
+  return df{h, __fsub_rn(t, __fsub_rn(h, s))};
 }
 
 // Glynn walk over [kb, ke) with double-float row sums: exact FP64 row sums at
@@ -349,7 +338,9 @@ __device__ __forceinline__ void walk_range_df(const double2* __restrict__ Acol, 
 #pragma unroll 1
     while (true) {
       df pr, pi;
-      prod_df2<N>(rh, rl, ih, il, pr, pi);
+      prod_dfv<N>(rh, rl, ih, il, pr, pi);
+      // to FP64 exactly (hi + lo fits), converted on the integer pipe: hardware
+      // conversions measured slower here (FP64-pipe dispatch stalls)
       const double xr = f32_to_f64_int(pr.h) + f32_to_f64_int(pr.l);
       const double xi = f32_to_f64_int(pi.h) + f32_to_f64_int(pi.l);
       const unsigned long long smask = (k & 1ull) << 63;  // (prod delta) = (-1)^(k & 1)
@@ -365,8 +356,8 @@ __device__ __forceinline__ void walk_range_df(const double2* __restrict__ Acol, 
 #pragma unroll
       for (int i = 0; i < N; i++) {
         const float4 x = col[i];
-        const df u = df_add(df{rh[i], rl[i]}, df{__fmul_rn(sg, x.x), __fmul_rn(sg, x.y)});
-        const df v = df_add(df{ih[i], il[i]}, df{__fmul_rn(sg, x.z), __fmul_rn(sg, x.w)});
+        const df u = df_add_signed(df{rh[i], rl[i]}, df{x.x, x.y}, sg);
+        const df v = df_add_signed(df{ih[i], il[i]}, df{x.z, x.w}, sg);
         rh[i] = u.h;
         rl[i] = u.l;
         ih[i] = v.h;

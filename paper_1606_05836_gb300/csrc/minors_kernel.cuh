@@ -90,7 +90,7 @@ __device__ __forceinline__ void minors_walk_df(const double2* Col0, const float4
 #pragma unroll 1
     while (true) {
       df pr, pi;
-      prod_df2<R>(rh, rl, ih, il, pr, pi);
+      prod_dfv<R>(rh, rl, ih, il, pr, pi);
       const double xr = f32_to_f64_int(pr.h) + f32_to_f64_int(pr.l);
       const double xi = f32_to_f64_int(pi.h) + f32_to_f64_int(pi.l);
       const unsigned long long smask = (k & 1ull) << 63;  // prod delta = (-1)^(k & 1)
@@ -113,8 +113,8 @@ __device__ __forceinline__ void minors_walk_df(const double2* Col0, const float4
 #pragma unroll
       for (int i = 0; i < R; i++) {
         const float4 x = col[i];
-        const df u = df_add(df{rh[i], rl[i]}, df{__fmul_rn(sg, x.x), __fmul_rn(sg, x.y)});
-        const df v = df_add(df{ih[i], il[i]}, df{__fmul_rn(sg, x.z), __fmul_rn(sg, x.w)});
+        const df u = df_add_signed(df{rh[i], rl[i]}, df{x.x, x.y}, sg);
+        const df v = df_add_signed(df{ih[i], il[i]}, df{x.z, x.w}, sg);
         rh[i] = u.h;
         rl[i] = u.l;
         ih[i] = v.h;

@@ -129,3 +129,37 @@ def test_fast_rungs_rank_one_n32(pg, prec, tol):
     want = math.factorial(32) * np.prod(u) * np.prod(v)
     got = val(pg.glynn(to_dev(A), prec=prec))
     assert abs(got - want) <= tol * abs(want), (prec, got, want)
+
+
+@pytest.mark.parametrize("n", [32, pytest.param(36, marks=pytest.mark.slow)])
+def test_ladder_at_sizes_beyond_the_oracle(pg, n):
+    """The ladder's inputs at n = 32 and 36, where the quad oracle is too slow to
+    run per test: every Glynn rung against R1 (FP64 products, double-double
+    accumulation; within 1e-12 of the oracle at n <= 28), and Ryser in FP64.
+    Gaussian inputs keep the 1e-10 bar.  The all-positive inputs cancel heavily
+    (the Glynn terms are far larger than the permanent): on all-ones + 1e-3 noise
+    FP64 Glynn and Ryser reproduce the paper's printed all-ones errors (Supp.
+    precision tables) within two decades, and the 0/1 inputs stay below that
+    band's Glynn bound."""
+    paper = {int(r["n"]): (float(r["bbfg_relerr"]), float(r["ryser_relerr"])) for r in read_tsv("precision_allones.tsv")}
+    print()
+    for kind in ("gaussian", "ones_noise", "bernoulli"):
+        A = refs_mod.make_input(kind, n, 0)
+        dA = to_dev(A)
+        ref = val(pg.glynn(dA, prec="fp64_dd"))
+        e = {p: abs(val(pg.glynn(dA, prec=p)) - ref) / abs(ref) for p in ("fp64", "fp32p_dd", "fp64_df", "fp32x2")}
+        e["ryser"] = abs(val(pg.ryser(dA)) - ref) / abs(ref)
+        print("n=%d %-10s vs R1: R0 %.2e  R2 %.2e  R3 %.2e  R4 %.2e  | Ryser FP64 %.2e" % (
+            n, kind, e["fp64"], e["fp32p_dd"], e["fp64_df"], e["fp32x2"], e["ryser"]))
+        assert e["fp32p_dd"] < 1e-2, (kind, e)
+        g, r = paper[n]
+        if kind == "gaussian":
+            assert e["fp64"] < REL_TOL and e["fp64_df"] < REL_TOL, (kind, e)
+            assert e["fp32x2"] < 1e-9, (kind, e)
+        else:
+            for p in ("fp64", "fp64_df", "fp32x2"):
+                assert e[p] < 100 * g, (kind, p, e[p], g)
+        if kind == "ones_noise":
+            print("      paper, all-ones: BB/FG %.2e  Ryser %.2e" % (g, r))
+            assert r / 100 < e["ryser"] < 100 * r, (e["ryser"], r)
+            assert e["ryser"] > 1e6 * e["fp64"]  # the paper's gap: Ryser loses many more digits
