@@ -233,3 +233,15 @@ def test_ryser_nw_vs_oracle(pg, n):
 def test_ryser_nw_fixed_checks(pg):
     assert val(pg.ryser_nw(to_dev(S.all_r(12, 1.0)))) == 479001600
     assert val(pg.ryser_nw(to_dev(S.ones_minus_identity(12)))) == 176214841
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp64_dd", "fp32p_dd", "fp64_df", "fp32x2"])
+def test_nonfinite_input_gives_nonfinite_output(pg, prec):
+    """A NaN or an infinity anywhere in A makes Per(A) non-finite (no silent finite value)."""
+    for bad in (np.nan, np.inf, -np.inf):
+        A = S.gaussian(12, 3)
+        A[4, 7] = bad
+        got = val(pg.glynn(to_dev(A), prec=prec))
+        assert not np.isfinite(got), (prec, bad, got)
+        if prec == "fp64":
+            assert not np.isfinite(val(pg.ryser(to_dev(A)))), bad
