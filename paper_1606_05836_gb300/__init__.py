@@ -29,11 +29,11 @@ import torch
 
 from . import _native
 from ._native import PERM_MAX_N, PRECISIONS, Opts, PermError
+from ._workspace import workspace as _workspace
 
-__all__ = ["glynn", "glynn_mult", "ryser", "ryser_nw", "glynn_range", "ryser_range", "workspace_size", "PermError", "PERM_MAX_N",
-           "PRECISIONS", "library", "batched", "BatchedPermanents", "grad", "PermAbs2", "prob"]
-
-_workspaces: dict = {}
+__all__ = ["glynn", "glynn_mult", "ryser", "ryser_nw", "glynn_range", "ryser_range", "workspace_size", "PermError",
+           "PERM_MAX_N", "PRECISIONS", "library", "batched", "BatchedPermanents", "grad", "PermAbs2", "prob",
+           "row_minors", "BosonSampler", "boson_sample"]
 
 
 def library():
@@ -70,15 +70,6 @@ def _stream_ptr(device) -> int:
 def workspace_size(n: int, **opts) -> int:
     o = _opts(**opts)
     return int(library().perm_workspace_size(int(n), ctypes.byref(o)))
-
-
-def _workspace(device, nbytes: int) -> torch.Tensor:
-    key = (device.index, _stream_ptr(device))
-    buf = _workspaces.get(key)
-    if buf is None or buf.numel() < nbytes:
-        buf = torch.empty(max(nbytes, 4096), dtype=torch.uint8, device=device)
-        _workspaces[key] = buf
-    return buf
 
 
 def _run(fname, A, extra, out_len, **opts):

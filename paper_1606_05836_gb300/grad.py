@@ -14,21 +14,9 @@ import torch
 
 from . import _native
 from ._native import Opts
+from ._workspace import workspace as _workspace
 
 PERM_GRAD_MAX_N = 32
-
-_workspaces: dict = {}
-
-
-def _workspace(device, nbytes):
-    key = (device.index, torch.cuda.current_stream(device).cuda_stream)
-    buf = _workspaces.get(key)
-    if buf is None or buf.numel() < nbytes:
-        buf = None
-        _workspaces.pop(key, None)
-        buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
-        _workspaces[key] = buf
-    return buf
 
 
 def grad(A: torch.Tensor, minor: bool = True, grad_abs2: bool = False, chunk_log2: int = 0, grid: int = 0):

@@ -21,20 +21,10 @@ import torch
 
 from . import _native
 from ._native import PRECISIONS, Opts
+from ._workspace import workspace as _workspace
 
 PERM_MINORS_MAX_K = 32
 BOSON_SAMPLE_MAX_N = 32
-
-_workspaces: dict = {}
-
-
-def _workspace(device, nbytes):
-    key = (device.index, torch.cuda.current_stream(device).cuda_stream)
-    buf = _workspaces.get(key)
-    if buf is None or buf.numel() < nbytes:
-        buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
-        _workspaces[key] = buf
-    return buf
 
 
 def _stream(dev):

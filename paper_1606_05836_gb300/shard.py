@@ -1,4 +1,5 @@
-"""Multi-GPU sharding of one large permanent over the Gray index range.
+"""Multi-GPU sharding: one large permanent over the Gray index range, and a
+batch of permanents by item.
 
 The split is Algorithm 2's (and Algorithm 1's) of arXiv 1606.05836: each rank
 takes one contiguous range of the iteration index, here of the Gray index
@@ -8,6 +9,11 @@ Each rank computes its un-normalised double-double partial sum on its own GPU
 — the paper's final MPI reduce of the per-process sums — is an all-gather of the
 32-byte partials, summed in rank order on every rank (deterministic), then scaled
 (Glynn: / 2^(n-1); Ryser: x (-1)^n).
+
+A batch (the many output patterns of one interferometer) shards by item: every
+rank derives the same assignment from the item sizes alone (largest work first,
+each item to the rank with the least work so far, work ~ 2^n), runs its items in
+one batched launch, and one all-gather returns every item's result to every rank.
 """
 from __future__ import annotations
 
@@ -86,5 +92,64 @@ def gpu_partial_fn(A: torch.Tensor, method: str = "glynn", **opts):
     def run(kb: int, ke: int):
         r = f(A, kb, ke, **opts).cpu()
         return complex(r[0].item()), complex(r[1].item())
+
+    return run
+
+
+def item_work(n: int, method: str = "glynn") -> int:
+    """Gray-code terms of one item: 2^(n-1) (Glynn) or 2^n (Ryser)."""
+    return 1 << (n - 1 if method == "glynn" else n) if n > 0 else 1
+
+
+def shard_items(ns, world: int, method: str = "glynn") -> list[list[int]]:
+    """Item indices per rank, balanced by Gray-code work.
+
+    Longest-processing-time order: items by decreasing work (ties by index), each
+    to the rank with the least assigned work (ties to the lower rank).  Depends on
+    the sizes only, so every rank computes the same lists.  Each list is in
+    increasing item order.
+    """
+    if world < 1:
+        raise ValueError("bad world")
+    order = sorted(range(len(ns)), key=lambda i: (-item_work(int(ns[i]), method), i))
+    load = [0] * world
+    out = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        out[r].append(i)
+        load[r] += item_work(int(ns[i]), method)
+    return [sorted(x) for x in out]
+
+
+def sharded_batched(mats, rank: int, world: int, run_fn, method: str = "glynn", group=None):
+    """Per(A_i) of every item, computed by item shards over the ranks.
+
+    run_fn(list_of_matrices) -> sequence of complex results for this rank's items
+    (e.g. a closure over ``paper_1606_05836_gb300.batched`` on this rank's GPU).
+    Returns the complex results of all items, in item order, on every rank.
+    """
+    ns = [int(A.shape[0]) for A in mats]
+    mine = shard_items(ns, world, method)[rank]
+    vals = list(run_fn([mats[i] for i in mine])) if mine else []
+    if world == 1:
+        return [complex(v) for v in vals]
+    import torch.distributed as dist
+
+    pieces = [None] * world
+    dist.all_gather_object(pieces, [(i, complex(v)) for i, v in zip(mine, vals)], group=group)
+    out = [None] * len(mats)
+    for piece in pieces:
+        for i, v in piece:
+            out[i] = v
+    return out
+
+
+def gpu_batched_fn(device, method: str = "glynn", **opts):
+    """run_fn for sharded_batched: the batched kernel on ``device``."""
+    from . import batched
+
+    def run(mats):
+        per, _ = batched(mats, method=method, device=device, **opts)
+        return per.cpu().tolist()
 
     return run

@@ -104,7 +104,7 @@ def check_against_oracle(U, inputs, alpha, u, got):
     assert near_ties <= 1
 
 
-@pytest.mark.parametrize("m,n,ns", [(8, 4, 40), (30, 8, 16), (64, 12, 6), (120, 16, 3)])
+@pytest.mark.parametrize("m,n,ns", [(8, 4, 40), (30, 8, 16), (64, 12, 6), (120, 16, 3), (1000, 16, 2)])
 @pytest.mark.parametrize("prec", ["fp64", "fp32x2"])
 def test_draws_match_oracle(pg, m, n, ns, prec):
     U = S.haar_unitary(m, 100 + m)

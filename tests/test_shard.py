@@ -10,7 +10,7 @@ import torch.multiprocessing as mp
 
 import oracle
 import synthetic as S
-from paper_1606_05836_gb300.shard import dd_sum, shard_range, sharded_permanent
+from paper_1606_05836_gb300.shard import dd_sum, item_work, shard_items, shard_range, sharded_batched, sharded_permanent
 
 
 def test_shard_range_partitions_exactly():
@@ -130,3 +130,69 @@ def test_a_dead_rank_fails_the_exchange_instead_of_hanging():
     assert not alive, "a rank hung"
     msg = q.get(timeout=10)
     assert msg.startswith("error"), msg
+
+
+def test_shard_items_covers_and_balances():
+    g = np.random.default_rng(3)
+    ns = [int(x) for x in g.integers(8, 25, size=500)]
+    for world in (1, 2, 3, 8):
+        parts = shard_items(ns, world)
+        flat = sorted(i for p in parts for i in p)
+        assert flat == list(range(len(ns)))
+        assert parts == shard_items(ns, world)  # every rank derives the same lists
+        loads = [sum(item_work(ns[i]) for i in p) for p in parts]
+        # greedy LPT: no rank exceeds the mean by more than the largest item
+        assert max(loads) <= sum(loads) / world + max(item_work(n) for n in ns)
+
+
+def _batched_rank_main(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    g = np.random.default_rng(11)
+    mats = [S.gaussian(int(n), 500 + i) for i, n in enumerate(g.integers(3, 11, size=17))]
+
+    def run(ms):
+        return [complex(oracle.perm_def(A).hi) for A in ms]
+
+    q.put((rank, sharded_batched(mats, rank, world, run)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_gloo_two_ranks_batched_by_item():
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_batched_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    got = dict(q.get(timeout=10) for _ in range(world))
+    g = np.random.default_rng(11)
+    mats = [S.gaussian(int(n), 500 + i) for i, n in enumerate(g.integers(3, 11, size=17))]
+    want = [complex(oracle.perm_def(A).hi) for A in mats]
+    assert got[0] == got[1] == want
+
+
+@pytest.mark.gpu
+def test_logical_item_shards_on_one_gpu():
+    """Three item shards, run one after another on one GPU, equal one batched launch bit for bit."""
+    import torch
+    from paper_1606_05836_gb300 import batched
+    from paper_1606_05836_gb300.shard import gpu_batched_fn
+    g = np.random.default_rng(12)
+    mats = [S.gaussian(int(n), 600 + i) for i, n in enumerate(g.integers(8, 21, size=40))]
+    whole, _ = batched(mats)
+    whole = whole.cpu().tolist()
+    fn = gpu_batched_fn(torch.device("cuda", 0))
+    parts = shard_items([A.shape[0] for A in mats], 3)
+    out = [None] * len(mats)
+    for p in parts:
+        for i, v in zip(p, fn([mats[i] for i in p])):
+            out[i] = v
+    assert out == whole
