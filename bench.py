@@ -356,6 +356,20 @@ def measure_forms(dev, plain_rate):
     tg32 = timed(lambda: pg.grad(G32))
     tf32 = timed(lambda: [pg.glynn(G32[b]) for b in range(2)])
     forms["adjoint_2_n32"] = {"terms_per_s": 2 * 2 ** 31 / tg32, "s": tg32, "cost_vs_plain_same_batch": tg32 / tf32}
+    # photon collisions at n = 28: the multiplicity expansion against the plain kernel on the expanded matrix
+    coll = {}
+    for mult in ([2, 1, 1, 1], [2, 2, 2, 1], [3, 2, 2, 2, 2, 1]):
+        mult = mult + [1] * (28 - sum(mult))
+        Bh = S.circular_gaussian((28, len(mult)), 2800 + len(mult), 1.0 / 28)
+        dB = torch.as_tensor(Bh).to(dev)
+        dE = torch.as_tensor(np.ascontiguousarray(np.repeat(Bh, mult, axis=1))).to(dev)
+        pg.glynn_mult(dB, mult)
+        tm = timed(lambda: pg.glynn_mult(dB, mult), reps=2)
+        tp = timed(lambda: pg.glynn(dE), reps=2)
+        a, b = complex(pg.glynn_mult(dB, mult).cpu().item()), complex(pg.glynn(dE).cpu().item())
+        key = "+".join(str(m) for m in mult if m > 1)
+        coll[key] = {"s": tm, "speedup_vs_expanded": tp / tm, "rel_diff_vs_expanded": abs(a - b) / abs(b)}
+    forms["collisions_n28"] = coll
     # row minors of a 31 x 32 matrix in one pass, against the forward kernel at n = 32
     M32 = torch.as_tensor(S.circular_gaussian((31, 32), 0, 1.0 / 32)).to(dev)
     pg.row_minors(M32)

@@ -80,3 +80,30 @@ def test_argument_errors_before_any_launch(lib):
                                 ctypes.byref(o), None) == -2
     assert lib.perm_ryser_range(ctypes.c_void_p(16), 4, 4, 5, 3, ctypes.c_void_p(32), ctypes.c_void_p(64), 1 << 20,
                                 ctypes.byref(o), None) == -2
+
+
+def test_argument_errors_of_minors_and_draws(lib):
+    """The row-minor and draw entry points reject bad arguments before touching the device."""
+    from paper_1606_05836_gb300._native import Opts
+    o = Opts(0, 0, 0, 0, 0)
+    p16, p32, p256 = ctypes.c_void_p(16), ctypes.c_void_p(32), ctypes.c_void_p(256)
+    assert lib.perm_row_minors(p16, 0, 1, 1, 0, p32, p256, 1 << 20, ctypes.byref(o), None) == -2
+    assert lib.perm_row_minors(p16, 33, 33, 1, 0, p32, p256, 1 << 20, ctypes.byref(o), None) == -2
+    assert lib.perm_row_minors(p16, 5, 5, -1, 0, p32, p256, 1 << 20, ctypes.byref(o), None) == -1
+    assert lib.perm_row_minors(p16, 5, 5, 1, 0, None, p256, 1 << 20, ctypes.byref(o), None) == -1
+    assert lib.perm_row_minors(None, 5, 5, 1, 0, p32, p256, 1 << 20, ctypes.byref(o), None) == -1
+    assert lib.perm_row_minors(p16, 5, 4, 1, 0, p32, p256, 1 << 20, ctypes.byref(o), None) == -1  # ldm < k
+    assert lib.perm_row_minors(p16, 5, 5, 0, 0, p32, p256, 1 << 20, ctypes.byref(o), None) == 0  # empty batch
+    ins = (ctypes.c_int32 * 3)(0, 1, 2)
+    rep = (ctypes.c_int32 * 3)(0, 1, 1)
+    far = (ctypes.c_int32 * 3)(0, 1, 9)
+    args = lambda m, n, inp, ns, u=p16: (u, m, m, n, inp, ns, p32, p32, p32, p256, 1 << 20, ctypes.byref(o), None)
+    assert lib.boson_sample(*args(8, 0, ins, 1)) == -2
+    assert lib.boson_sample(*args(40, 33, ins, 1)) == -2
+    assert lib.boson_sample(*args(2, 3, ins, 1)) == -1      # fewer modes than photons
+    assert lib.boson_sample(*args(8, 3, rep, 1)) == -1      # two photons in one input mode
+    assert lib.boson_sample(*args(8, 3, far, 1)) == -1      # input mode out of range
+    assert lib.boson_sample(*args(8, 3, ins, -1)) == -1
+    assert lib.boson_sample(*args(8, 3, ins, 0)) == 0       # no draws: nothing to do
+    assert lib.boson_sample(*args(8, 3, ins, 2, u=None)) == -1
+    assert lib.boson_sample(*args(8, 3, None, 2)) == -1
