@@ -172,6 +172,33 @@ __global__ void __launch_bounds__(256, 1) fwd_kernel(FwdArgs a) {
     walk_range_df<N>(Acol, StepF, NP, kb, ke, CH, ar, ai);
     sr = dd{ar, 0.0};
     si = dd{ai, 0.0};
+  } else if (a.kind == KIND_GLYNN_MULT && a.mult.nfree >= 5 && a.k_begin == 0) {
+    // Warp-aligned split: each class's 2^nfree local indices are laid out
+    // lane-major (lane l owns [l F, (l+1) F), F = 2^(nfree-5)), and warp w takes
+    // a contiguous run of the class-by-class offsets o in [0, F).  All 32 lanes
+    // of a warp then walk equal-length ranges of the same class and cross class
+    // boundaries together (no lane restarts a chunk while the others wait), and
+    // every lane's share differs by at most one term.
+    sr = dd{0.0, 0.0};
+    si = dd{0.0, 0.0};
+    const int nfree = a.mult.nfree;
+    const uint64_t F = 1ull << (nfree - 5);
+    const uint64_t U = a.k_end >> 5;  // class-by-class offsets: classes x F
+    const uint64_t W = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t w = T >> 5;
+    const uint64_t lane = T & 31u;
+    const uint64_t q = U / W, r = U % W;
+    uint64_t u = w * q + (w < r ? w : r);
+    const uint64_t u1 = u + q + (w < r ? 1 : 0);
+    while (u < u1) {
+      const uint64_t c = u >> (nfree - 5);
+      const uint64_t ob = u - (c << (nfree - 5));
+      const uint64_t oe = (u1 - (c << (nfree - 5)) < F) ? u1 - (c << (nfree - 5)) : F;
+      const uint64_t base = (c << nfree) + lane * F;
+      walk_range<N, PREC, TUNE, false>(Acol, Step, nullptr, &a.mult, &sr, &si, NP, a.kind, base + ob, base + oe, CH,
+                                       nz, ar, ai, cr, ci);
+      u = (c << (nfree - 5)) + oe;
+    }
   } else if (a.kind == KIND_GLYNN_MULT) {
     sr = dd{0.0, 0.0};
     si = dd{0.0, 0.0};

@@ -93,3 +93,15 @@ def test_prob_bunching_and_collisions(pg):
         pw, perw = oracle.prob(U, s, t)
         assert perw.rel_err(per) < REL_TOL
         assert abs(p - pw) <= 1e-9 * pw
+
+
+@pytest.mark.parametrize("mult", [[2, 2, 2] + [1] * 14, [3, 2, 2, 1] + [1] * 12])
+@pytest.mark.parametrize("opts", [{}, {"grid": 2}, {"grid": 997}, {"grid": 5, "chunk_log2": 3}])
+def test_mult_warp_aligned_split_vs_oracle(pg, mult, opts):
+    """>= 5 free columns: the warp-aligned class layout (every warp's lanes in one
+    class at a time), with a ragged warp split and short chunks, against the oracle."""
+    n, g = sum(mult), len(mult)
+    B = S.circular_gaussian((n, g), 3000 + g, 1.0 / n)
+    want = oracle.ryser(expand(B, mult))
+    got = val(pg.glynn_mult(to_dev(B), mult, **opts))
+    assert want.rel_err(got) < REL_TOL, (mult, opts, got, want.hi)
