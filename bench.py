@@ -375,9 +375,10 @@ def measure_forms(dev, plain_rate):
     pg.row_minors(M32)
     tm = timed(lambda: pg.row_minors(M32))
     forms["row_minors_k32"] = {"terms_per_s": 2 ** 31 / tm, "s": tm, "cost_vs_glynn_n32": tm * base / 2 ** 31}
-    pg.row_minors(M32, prec="fp32x2")
-    tm4 = timed(lambda: pg.row_minors(M32, prec="fp32x2"))
-    forms["row_minors_k32_fp32x2"] = {"terms_per_s": 2 ** 31 / tm4, "s": tm4, "cost_vs_glynn_n32": tm4 * base / 2 ** 31}
+    for rp in ("fp64_df", "fp32x2"):
+        pg.row_minors(M32, prec=rp)
+        tmr = timed(lambda: pg.row_minors(M32, prec=rp))
+        forms["row_minors_k32_" + rp] = {"terms_per_s": 2 ** 31 / tmr, "s": tmr, "cost_vs_glynn_n32": tmr * base / 2 ** 31}
     # boson-sampling draws: 16 draws of 24 photons in the 1000-mode unitary (one graph replay)
     m, n, ns = 1000, 24, 16
     smp, alpha, uu = sampler_case(pg, U, n, ns, 5, dev)
@@ -398,17 +399,18 @@ def measure_forms(dev, plain_rate):
                                            "cost_per_draw_in_glynn_n24": ts / ns / t24,
                                            "launches_per_replay": 2 * n - 1,
                                            "draws_equal_oracle_m30_n8": same}
-    smp4, _, _ = sampler_case(pg, U, n, ns, 5, dev, prec="fp32x2")
-    smp4.capture()
-    smp4.replay()
-    ts4 = timed(smp4.replay, reps=2)
-    s304, _, _ = sampler_case(pg, U30, 8, 4, 6, dev, prec="fp32x2")
-    got4 = s304.run().cpu().numpy()
-    same4 = "%d/4" % sum(int(list(got4[i]) == rs["draws"][i]) for i in range(4))
-    forms["boson_sample_m1000_n24_x16_fp32x2"] = {"draws_per_s": ns / ts4, "s_per_replay": ts4,
-                                                  "terms_per_s": ns * (2 ** n - 2) / ts4,
-                                                  "cost_per_draw_in_glynn_n24": ts4 / ns / t24,
-                                                  "draws_equal_oracle_m30_n8": same4}
+    for rp in ("fp64_df", "fp32x2"):
+        smp4, _, _ = sampler_case(pg, U, n, ns, 5, dev, prec=rp)
+        smp4.capture()
+        smp4.replay()
+        ts4 = timed(smp4.replay, reps=2)
+        s304, _, _ = sampler_case(pg, U30, 8, 4, 6, dev, prec=rp)
+        got4 = s304.run().cpu().numpy()
+        same4 = "%d/4" % sum(int(list(got4[i]) == rs["draws"][i]) for i in range(4))
+        forms["boson_sample_m1000_n24_x16_" + rp] = {"draws_per_s": ns / ts4, "s_per_replay": ts4,
+                                                     "terms_per_s": ns * (2 ** n - 2) / ts4,
+                                                     "cost_per_draw_in_glynn_n24": ts4 / ns / t24,
+                                                     "draws_equal_oracle_m30_n8": same4}
     return forms
 
 

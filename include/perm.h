@@ -236,7 +236,8 @@ int perm_glynn_noalloc(const perm_c128* dA, int n, int lda, perm_c128* dOut, con
  * of arXiv 1606.05836 is linear in x and m_j is the coefficient of x_j,
  *     m_j = 2^-(k-1) sum_delta (prod delta) delta_j prod_{i<k-1} (sum_l delta_l M_il).
  * (The paper has no such routine; the boson sampler below needs it.)  opts->prec
- * PERM_FP64 (default) or PERM_FP32X2 (the walk in double-float, as for perm_glynn).
+ * PERM_FP64 (default), PERM_FP64_DF (double-float products of the FP64 row sums)
+ * or PERM_FP32X2 (the walk in double-float), as for perm_glynn.
  *
  * dM:    batch matrices (device, complex128, row-major, k-1 rows of k entries,
  *        row stride ldm >= k); matrix b at dM + b*strideM elements.
@@ -273,7 +274,8 @@ int perm_row_minors(const perm_c128* dM, int k, int ldm, int batch, int64_t stri
  *           has all n entries -1.
  * dWork:    256-byte-aligned, boson_sample_workspace_size(m, n, nsamples) bytes
  *           (O(nsamples x (16 m + 8 n) + partials)).
- * opts->prec PERM_FP64 (default) or PERM_FP32X2 selects the row minors' arithmetic.
+ * opts->prec PERM_FP64 (default), PERM_FP64_DF or PERM_FP32X2 selects the row
+ * minors' arithmetic.
  * 1 <= n <= BOSON_SAMPLE_MAX_N, n <= m.  2n - 1 kernel launches, all on
  * `stream`, no host synchronisation (the call may be captured in a CUDA graph
  * once the workspace exists). */

@@ -1,5 +1,5 @@
-// Explicit instantiations of the row-minor kernel (FP64 and R4), compiled once
-// per group of sizes (-DPERM_PART=0..3).
+// Explicit instantiations of the row-minor kernel (FP64, R3 and R4), compiled
+// once per group of sizes (-DPERM_PART=0..3).
 #include "minors_kernel.cuh"
 
 #ifndef PERM_PART
@@ -27,20 +27,26 @@ static int launch_one_minors(const MinorsArgs& a, int grid, cudaStream_t s) {
   return (int)cudaGetLastError();
 }
 
+template <int K, int PREC>
+static int occupancy_one_minors(int* out) {
+  int e = minors_smem_attr<K, PREC>();
+  if (e) return e;
+  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, minors_kernel<K, PREC>, MINORS_BLOCK,
+                                                            minors_smem_bytes(K));
+}
+
 template <int K>
 int launch_minors(const MinorsArgs& a, int prec, int grid, cudaStream_t s) {
-  return prec == 4 ? launch_one_minors<K, 4>(a, grid, s) : launch_one_minors<K, 0>(a, grid, s);
+  if (prec == 4) return launch_one_minors<K, 4>(a, grid, s);
+  if (prec == 3) return launch_one_minors<K, 3>(a, grid, s);
+  return launch_one_minors<K, 0>(a, grid, s);
 }
 
 template <int K>
 int minors_blocks_per_sm(int prec, int* out) {
-  int e = prec == 4 ? minors_smem_attr<K, 4>() : minors_smem_attr<K, 0>();
-  if (e) return e;
-  if (prec == 4)
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, minors_kernel<K, 4>, MINORS_BLOCK,
-                                                              minors_smem_bytes(K));
-  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, minors_kernel<K, 0>, MINORS_BLOCK,
-                                                            minors_smem_bytes(K));
+  if (prec == 4) return occupancy_one_minors<K, 4>(out);
+  if (prec == 3) return occupancy_one_minors<K, 3>(out);
+  return occupancy_one_minors<K, 0>(out);
 }
 
 #define PERM_MINST(K)                                                       \

@@ -44,6 +44,8 @@ struct MinorsArgs {
 
 __device__ __forceinline__ int clamp_index(int x, int lim) { return (x >= 0 && x < lim) ? x : 0; }
 
+// R3 (PREC = 3): FP64 row sums and accumulation, the product of the K-1 row sums
+// in double-float on the FP32 pipe (as the forward kernel's R3).
 // R4 (PREC = 4): double-float row sums and products on the FP32 pipe (as the
 // forward kernel's R4), the doubled columns rounded to double-float in shared
 // memory and the row sums re-split from FP64 sums of those same columns at every
@@ -234,7 +236,13 @@ __global__ void __launch_bounds__(MINORS_BLOCK, 2) minors_kernel(MinorsArgs a) {
 #pragma unroll 1
     while (true) {
       const unsigned long long smask = (k & 1ull) << 63;  // prod delta = (-1)^(k & 1)
-      if (R > 0) {
+      if constexpr (PREC == 3 && R > 1) {
+        // R3: double-float product of the FP64 row sums (FP64 updates and accumulation)
+        double pr, pi;
+        prod_df<R>(vr, vi, pr, pi);
+        sr += xor_sign(pr, smask);
+        si += xor_sign(pi, smask);
+      } else if (R > 0) {
         term_r0<(R > 0 ? R : 1), 3>(vr, vi, smask, sr, si, nz);
       } else {
         sr += xor_sign(1.0, smask);

@@ -260,11 +260,11 @@ int dispatch_minors_occupancy(int k, int prec, int* out) {
 // Resident blocks per SM of minors_kernel<k>, cached per device.
 constexpr int MAX_DEVICES = 64;
 std::mutex g_occ_mu;
-int g_occ[MAX_DEVICES][2][MINORS_MAX_K + 1];
+int g_occ[MAX_DEVICES][3][MINORS_MAX_K + 1];
 int g_sms[MAX_DEVICES];
 
 int minors_wave(int k, int prec, long long* wave) {
-  const int pi = prec == PERM_FP32X2 ? 1 : 0;
+  const int pi = prec == PERM_FP32X2 ? 2 : (prec == PERM_FP64_DF ? 1 : 0);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return sfail((int)e);
@@ -292,10 +292,10 @@ struct MinorsPlan {
   uint64_t per_q, per_r;
 };
 
-// FP64 (R0) or R4; R4's default chunk is 2^10 as in the forward kernel
+// FP64 (R0), R3 or R4; R4's default chunk is 2^10 as in the forward kernel
 int read_minors_opts(const perm_opts* o, int* prec, int* chunk, int* grid) {
   *prec = o ? o->prec : PERM_FP64;
-  if (*prec != PERM_FP64 && *prec != PERM_FP32X2) return PERM_EINVAL;
+  if (*prec != PERM_FP64 && *prec != PERM_FP64_DF && *prec != PERM_FP32X2) return PERM_EINVAL;
   if (o && o->block != 0 && o->block != MINORS_BLOCK) return PERM_EINVAL;
   *chunk = (o && o->chunk_log2) ? o->chunk_log2 : (*prec == PERM_FP32X2 ? 10 : 12);
   if (*chunk < 1 || *chunk > 30) return PERM_EINVAL;

@@ -32,17 +32,17 @@ def _stream(dev):
 
 
 def _prec(prec) -> int:
-    if prec not in ("fp64", "fp32x2"):
-        raise ValueError("row minors and draws support prec 'fp64' or 'fp32x2'")
+    if prec not in ("fp64", "fp64_df", "fp32x2"):
+        raise ValueError("row minors and draws support prec 'fp64', 'fp64_df' or 'fp32x2'")
     return PRECISIONS[prec]
 
 
 def row_minors(M: torch.Tensor, prec: str = "fp64", chunk_log2: int = 0, grid: int = 0) -> torch.Tensor:
     """m_j = Per(M without column j) for M of shape (k-1, k) or (batch, k-1, k).
 
-    Returns complex128 of shape (k,) or (batch, k).  ``prec`` "fp32x2" runs the
-    walk in double-float on the FP32 pipe (R4).  ``grid`` > 0 fixes the blocks
-    per matrix.
+    Returns complex128 of shape (k,) or (batch, k).  ``prec`` "fp64_df" takes the
+    products in double-float on the FP32 pipe (R3: FP64 row sums); "fp32x2" runs
+    the whole walk in double-float (R4).  ``grid`` > 0 fixes the blocks per matrix.
     """
     lib = _native.load()
     if not isinstance(M, torch.Tensor) or not M.is_cuda or M.dtype != torch.complex128:
@@ -79,8 +79,10 @@ class BosonSampler:
     permutation of 0..n-1) and float64 (nsamples, n) uniforms in [0, 1), both on
     U's device, and returns the int32 (nsamples, n) drawn output modes (draw
     order; -1 for a draw with invalid inputs or a step of zero total weight).
-    ``prec`` "fp32x2" computes the row minors in double-float (R4, ~4x faster;
-    weights to ~1e-12, which can change a draw only at a near-tie).
+    ``prec`` "fp64_df" (R3: FP64 row sums, double-float products) or "fp32x2"
+    (R4: the whole walk in double-float) compute the row minors faster; their
+    weights differ from FP64's by ~1e-13 .. 1e-12, which can change a draw only
+    at a near-tie.
     """
 
     def __init__(self, U: torch.Tensor, inputs, nsamples: int, prec: str = "fp64", chunk_log2: int = 0,

@@ -39,7 +39,7 @@ def close_vec(got, want, tol=REL_TOL):
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("k", [2, 3, 5, 9, 16, 21])
-@pytest.mark.parametrize("opts", [{}, {"grid": 3, "chunk_log2": 3}, {"prec": "fp32x2"},
+@pytest.mark.parametrize("opts", [{}, {"grid": 3, "chunk_log2": 3}, {"prec": "fp64_df"}, {"prec": "fp32x2"},
                                   {"prec": "fp32x2", "grid": 5, "chunk_log2": 4}])
 def test_row_minors_vs_oracle(pg, k, opts):
     M = S.circular_gaussian((k - 1, k), 4000 + k, 1.0 / k)
@@ -65,7 +65,7 @@ def test_row_minors_batch(pg):
 
 
 @pytest.mark.parametrize("k", [24, 32])
-@pytest.mark.parametrize("prec", ["fp64", "fp32x2"])
+@pytest.mark.parametrize("prec", ["fp64", "fp64_df", "fp32x2"])
 def test_row_minors_rank_one_full_size(pg, k, prec):
     """M = u v^T: m_j = (k-1)! prod u prod_{l != j} v_l (closed form at the largest size)."""
     g = np.random.default_rng(k)
@@ -78,7 +78,7 @@ def test_row_minors_rank_one_full_size(pg, k, prec):
     # have one common size: the bound is normwise (a minor with a large |v_j|
     # excluded is small and carries the same absolute error)
     scale = np.max(np.abs(want))
-    tol = REL_TOL if prec == "fp64" else 1e-9  # R4's stated bound on extreme cancellation
+    tol = 1e-9 if prec == "fp32x2" else REL_TOL  # R4's stated bound on extreme cancellation
     for j in range(k):
         assert abs(got[j] - want[j]) <= tol * scale, (j, got[j], want[j])
 
@@ -105,7 +105,7 @@ def check_against_oracle(U, inputs, alpha, u, got):
 
 
 @pytest.mark.parametrize("m,n,ns", [(8, 4, 40), (30, 8, 16), (64, 12, 6), (120, 16, 3), (1000, 16, 2)])
-@pytest.mark.parametrize("prec", ["fp64", "fp32x2"])
+@pytest.mark.parametrize("prec", ["fp64", "fp64_df", "fp32x2"])
 def test_draws_match_oracle(pg, m, n, ns, prec):
     U = S.haar_unitary(m, 100 + m)
     g = np.random.default_rng(m)
@@ -138,7 +138,7 @@ def test_draw_histogram_matches_eq1(pg):
     assert dof >= 20 and chi2 < 80.0, (chi2, dof)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32x2"])
+@pytest.mark.parametrize("prec", ["fp64", "fp64_df", "fp32x2"])
 def test_hong_ou_mandel_32_photons(pg, prec):
     """16 beam splitters side by side, one photon in every mode: every pair bunches."""
     m = n = 32
