@@ -2,8 +2,9 @@
 //
 // dPer/da_ij = 2^-(n-1) sum_delta (prod delta) delta_j prod_{k != i} v_k(delta),
 // v_i = sum_j delta_j a_ij.  Per term, q_i = prod_{k != i} v_k comes from one
-// suffix pass (stored per lane in shared memory) and one prefix pass — 3(n-2)
-// complex multiplies, no division (a row sum may be exactly zero).  With
+// suffix pass (stored per lane in shared memory) and one prefix pass — 2(n-2)
+// complex multiplies plus one complex multiply-add per row that forms q_i and
+// adds it to S_i at once, no division (a row sum may be exactly zero).  With
 // w_i = (prod delta) q_i, G_ij = sum over terms of w_i delta_j is accumulated at
 // O(n) per term: S_i = running sum of w_i (shared memory) and H_ij = G_ij -
 // delta_j S_i, which changes only when the Gray code flips column j
@@ -187,33 +188,30 @@ __global__ void __launch_bounds__(GRAD_BLOCK, 1) grad_kernel(GradArgs a) {
           cmul_inplace<3>(pr, pi, vr[i], vi[i], nz);
           suf[i * B] = make_double2(pr, pi);
         }
-        // prefix pass: q_i = (v_0 ... v_{i-1}) suf_{i+1}
-        double qr = pr, qi = pi;  // q_0 = suf_1
-        double2 s0 = S[0];
-        s0.x = fma(sgn, qr, s0.x);
-        s0.y = fma(sgn, qi, s0.y);
+        // prefix pass, carrying the term's sign: e = (prod delta) v_0 ... v_{i-1}, so
+        // S_i += (prod delta) q_i = e suf_{i+1} is one complex multiply-add (4 FMAs)
+        double2 s0 = S[0];  // q_0 = suf_1
+        s0.x = fma(sgn, pr, s0.x);
+        s0.y = fma(sgn, pi, s0.y);
         S[0] = s0;
-        double er = vr[0], ei = vi[0];  // prefix v_0 ... v_{i-1}
+        double er = xor_sign(vr[0], smask), ei = xor_sign(vi[0], smask);
 #pragma unroll
         for (int i = 1; i < N - 1; i++) {
           const double2 sf = suf[(i + 1) * B];
-          qr = er;
-          qi = ei;
-          cmul_inplace<3>(qr, qi, sf.x, sf.y, nz);
           double2 si = S[i * B];
-          si.x = fma(sgn, qr, si.x);
-          si.y = fma(sgn, qi, si.y);
+          si.x = fma(er, sf.x, si.x);
+          si.x = fma(-ei, sf.y, si.x);
+          si.y = fma(er, sf.y, si.y);
+          si.y = fma(ei, sf.x, si.y);
           S[i * B] = si;
           cmul_inplace<3>(er, ei, vr[i], vi[i], nz);
         }
-        // q_{N-1} = prefix of all but the last row
+        // q_{N-1} = prefix of all but the last row (e already carries the sign)
         double2 sl = S[(N - 1) * B];
-        sl.x = fma(sgn, er, sl.x);
-        sl.y = fma(sgn, ei, sl.y);
+        sl.x += er;
+        sl.y += ei;
         S[(N - 1) * B] = sl;
         // forward term: (prod delta) * prefix * v_{N-1}
-        er = xor_sign(er, smask);
-        ei = xor_sign(ei, smask);
         ar = fma(er, vr[N - 1], ar);
         ar = fma(-ei, vi[N - 1], ar);
         ai = fma(er, vi[N - 1], ai);
