@@ -21,8 +21,10 @@ evaluates, and which passage of arXiv 1606.05836 it follows:
 * :func:`ryser_int`     -- Eq. (S1) exactly, integers modulo 2^128.
 * :func:`minors`        -- Per of every (n-1)x(n-1) minor = dPer/da_ij.
 * :func:`prob`          -- Eq. (1), |Per(U_ST)|^2 / (prod s_i! prod t_j!).
+* :mod:`oracle.sampler` -- row minors and boson-sampling draws from Eq. (1) by the
+                           chain rule over the photons (numpy over the functions above).
 
-Parity pins: tests/test_oracle_pins.py.
+Parity pins: tests/test_oracle_pins.py, tests/test_sampler_oracle.py.
 """
 from __future__ import annotations
 
