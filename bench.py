@@ -269,7 +269,10 @@ def run_reference(args):
 # the other forms, each against the plain form on the same GPU
 # ---------------------------------------------------------------------------
 def measure_forms(dev, plain_rate):
-    """Batched (graph replay), compensated rungs R1/R2 and the adjoint, with errors."""
+    """The other forms of the method on the same GPU: precision rungs, the batched
+    form (graph replay), the adjoint, photon collisions, row minors and
+    boson-sampling draws, each with its parity figure.  A failing section is
+    reported as "<name>_error" instead of ending the run."""
     import math
 
     import numpy as np
@@ -294,123 +297,136 @@ def measure_forms(dev, plain_rate):
         return best
 
     forms = {}
-    # precision ladder: rates at n = 32 (Gaussian var 1/n^2), errors at n = 20 vs the quad oracle
-    A32 = torch.as_tensor(S.gaussian(32, 0)).to(dev)
-    A20h = S.gaussian(20, 0)
-    A20 = torch.as_tensor(A20h).to(dev)
-    r20 = refs["glynn_gaussian_n20"]
-    for prec in ("fp64", "fp64_dd", "fp32p_dd", "fp64_df", "fp32x2"):
-        pg.glynn(A32, prec=prec)
-        t = timed(lambda: pg.glynn(A32, prec=prec))
-        err = ref_rel_err(r20, A20h, complex(pg.glynn(A20, prec=prec).cpu().item()))
-        forms["glynn_n32_" + prec] = {"terms_per_s": 2 ** 31 / t, "vs_plain_glynn": None, "rel_err_n20_vs_oracle": err}
-    base = forms["glynn_n32_fp64"]["terms_per_s"]
-    for k in list(forms):
-        forms[k]["vs_plain_glynn"] = forms[k]["terms_per_s"] / base
-    # batched: 4096 output patterns of one Haar 1000 x 1000 unitary, n in 8..24, 20 % collisions
-    U = S.haar_unitary(1000, 0)
-    mats, ns, rows, cols, collide = S.batch_patterns(U, 4096, 8, 24, 1)
-    scale = [1.0 / float(np.prod([math.factorial(int(x)) for x in np.bincount(c)])) for c in cols]
-    bp = B.BatchedPermanents(mats, method="glynn", scale=scale)
-    tuned = bp.autotune(candidates=[(9, 128), (11, 64), (11, 128), (13, 128)], reps=1)
-    bp.capture()
-    bp.replay()
-    t = timed(bp.replay, reps=3)
-    terms = int(sum(2 ** (int(n) - 1) for n in ns))
-    per = bp.out.cpu().numpy()
-    # sampled parity of the batched kernel: the 8 stored items (n <= 14) of this batch, with their oracle values
-    items = refs["batched_items"]
-    pick = [unflat(r["matrix"], r["n"], r["n"]) for r in items]
-    per8, _ = pg.batched(pick, method="glynn")
-    per8 = per8.cpu().numpy()
-    berr = max(ref_rel_err(r, pick[i], complex(per8[i])) for i, r in enumerate(items))
-    # the same batch in R4 (double-float walk on the FP32 pipe), same launch shape
-    bp4 = B.BatchedPermanents(mats, method="glynn", scale=scale, prec="fp32x2", unit_log2=tuned["unit_log2"],
-                              block=tuned["block"])
-    bp4.capture()
-    bp4.replay()
-    t4 = timed(bp4.replay, reps=3)
-    per8_4, _ = pg.batched(pick, method="glynn", prec="fp32x2")
-    per8_4 = per8_4.cpu().numpy()
-    berr4 = max(ref_rel_err(r, pick[i], complex(per8_4[i])) for i, r in enumerate(items))
-    forms["batched_4096_n8-24_fp32x2"] = {"terms_per_s": terms / t4, "perms_per_s": len(mats) / t4,
-                                         "s_per_replay": t4, "vs_fp64_batch": t / t4,
-                                         "max_rel_err_sampled_vs_oracle": berr4}
-    forms["batched_4096_n8-24"] = {"terms_per_s": terms / t, "perms_per_s": len(mats) / t, "s_per_replay": t,
-                                   "vs_plain_glynn": terms / t / base, "collision_items": int(collide.sum()),
-                                   "tuned": {"unit_log2": tuned["unit_log2"], "block": tuned["block"]},
-                                   "max_rel_err_sampled_vs_oracle": berr}
-    # adjoint: batch of 64 Gaussian matrices at n = 24
-    G = torch.as_tensor(np.stack([S.gaussian(24, b) for b in range(64)])).to(dev)
-    pg.grad(G[:1])
-    tg = timed(lambda: pg.grad(G))
-    tf = timed(lambda: [pg.glynn(G[b]) for b in range(64)])
-    _, _, M, _ = pg.grad(G[:1])
-    A0 = G[0].cpu().numpy()
-    P0 = complex(pg.glynn(G[0]).cpu().item())
-    lap = float(np.max(np.abs(np.sum(A0 * M[0].cpu().numpy(), axis=1) - P0)) / abs(P0))
-    forms["adjoint_64_n24"] = {"terms_per_s": 64 * 2 ** 23 / tg, "s": tg, "cost_vs_plain_same_batch": tg / tf,
-                               "laplace_identity_rel_err": lap}
-    # adjoint at n = 32 on a batch of 2 (64 would take minutes)
-    G32 = torch.as_tensor(np.stack([S.gaussian(32, b) for b in range(2)])).to(dev)
-    tg32 = timed(lambda: pg.grad(G32))
-    tf32 = timed(lambda: [pg.glynn(G32[b]) for b in range(2)])
-    forms["adjoint_2_n32"] = {"terms_per_s": 2 * 2 ** 31 / tg32, "s": tg32, "cost_vs_plain_same_batch": tg32 / tf32}
-    # photon collisions at n = 28: the multiplicity expansion against the plain kernel on the expanded matrix
-    coll = {}
-    for mult in ([2, 1, 1, 1], [2, 2, 2, 1], [3, 2, 2, 2, 2, 1]):
-        mult = mult + [1] * (28 - sum(mult))
-        Bh = S.circular_gaussian((28, len(mult)), 2800 + len(mult), 1.0 / 28)
-        dB = torch.as_tensor(Bh).to(dev)
-        dE = torch.as_tensor(np.ascontiguousarray(np.repeat(Bh, mult, axis=1))).to(dev)
-        pg.glynn_mult(dB, mult)
-        tm = timed(lambda: pg.glynn_mult(dB, mult), reps=2)
-        tp = timed(lambda: pg.glynn(dE), reps=2)
-        a, b = complex(pg.glynn_mult(dB, mult).cpu().item()), complex(pg.glynn(dE).cpu().item())
-        key = "+".join(str(m) for m in mult if m > 1)
-        coll[key] = {"s": tm, "speedup_vs_expanded": tp / tm, "rel_diff_vs_expanded": abs(a - b) / abs(b)}
-    forms["collisions_n28"] = coll
-    # row minors of a 31 x 32 matrix in one pass, against the forward kernel at n = 32
-    M32 = torch.as_tensor(S.circular_gaussian((31, 32), 0, 1.0 / 32)).to(dev)
-    pg.row_minors(M32)
-    tm = timed(lambda: pg.row_minors(M32))
-    forms["row_minors_k32"] = {"terms_per_s": 2 ** 31 / tm, "s": tm, "cost_vs_glynn_n32": tm * base / 2 ** 31}
-    for rp in ("fp64_df", "fp32x2"):
-        pg.row_minors(M32, prec=rp)
-        tmr = timed(lambda: pg.row_minors(M32, prec=rp))
-        forms["row_minors_k32_" + rp] = {"terms_per_s": 2 ** 31 / tmr, "s": tmr, "cost_vs_glynn_n32": tmr * base / 2 ** 31}
-    # boson-sampling draws: 16 draws of 24 photons in the 1000-mode unitary (one graph replay)
-    m, n, ns = 1000, 24, 16
-    smp, alpha, uu = sampler_case(pg, U, n, ns, 5, dev)
-    smp.capture()
-    smp.replay()
-    ts = timed(smp.replay, reps=2)
-    A24 = torch.as_tensor(S.gaussian(24, 0)).to(dev)
-    pg.glynn(A24)
-    t24 = timed(lambda: pg.glynn(A24), reps=2)
-    # sampled parity: 4 draws of 8 photons in 30 modes against the oracle's stored draws
-    rs = refs["sampler_m30_n8"]
-    U30 = unflat(rs["U"], 30, 30)
-    s30, a30, u30 = sampler_case(pg, U30, 8, 4, 6, dev)
-    got = s30.run().cpu().numpy()
-    same = "%d/4" % sum(int(list(got[i]) == rs["draws"][i]) for i in range(4))
-    forms["boson_sample_m1000_n24_x16"] = {"draws_per_s": ns / ts, "s_per_replay": ts,
-                                           "terms_per_s": ns * (2 ** n - 2) / ts,
-                                           "cost_per_draw_in_glynn_n24": ts / ns / t24,
-                                           "launches_per_replay": 2 * n - 1,
-                                           "draws_equal_oracle_m30_n8": same}
-    for rp in ("fp64_df", "fp32x2"):
-        smp4, _, _ = sampler_case(pg, U, n, ns, 5, dev, prec=rp)
-        smp4.capture()
-        smp4.replay()
-        ts4 = timed(smp4.replay, reps=2)
-        s304, _, _ = sampler_case(pg, U30, 8, 4, 6, dev, prec=rp)
-        got4 = s304.run().cpu().numpy()
-        same4 = "%d/4" % sum(int(list(got4[i]) == rs["draws"][i]) for i in range(4))
-        forms["boson_sample_m1000_n24_x16_" + rp] = {"draws_per_s": ns / ts4, "s_per_replay": ts4,
-                                                     "terms_per_s": ns * (2 ** n - 2) / ts4,
-                                                     "cost_per_draw_in_glynn_n24": ts4 / ns / t24,
-                                                     "draws_equal_oracle_m30_n8": same4}
+    ctx = {"base": plain_rate}
+
+    def ladder():
+        # precision ladder: rates at n = 32 (Gaussian var 1/n^2), errors at n = 20 vs a stored oracle value
+        A32 = torch.as_tensor(S.gaussian(32, 0)).to(dev)
+        A20h = S.gaussian(20, 0)
+        A20 = torch.as_tensor(A20h).to(dev)
+        r20 = refs["glynn_gaussian_n20"]
+        rungs = {}
+        for prec in ("fp64", "fp64_dd", "fp32p_dd", "fp64_df", "fp32x2"):
+            pg.glynn(A32, prec=prec)
+            t = timed(lambda: pg.glynn(A32, prec=prec))
+            err = ref_rel_err(r20, A20h, complex(pg.glynn(A20, prec=prec).cpu().item()))
+            rungs[prec] = {"terms_per_s": 2 ** 31 / t, "vs_plain_glynn": None, "rel_err_n20_vs_oracle": err}
+        ctx["base"] = rungs["fp64"]["terms_per_s"]
+        for prec, v in rungs.items():
+            v["vs_plain_glynn"] = v["terms_per_s"] / ctx["base"]
+            forms["glynn_n32_" + prec] = v
+
+    def batched():
+        # 4096 output patterns of one Haar 1000 x 1000 unitary, n in 8..24, 20 % collisions
+        U = S.haar_unitary(1000, 0)
+        ctx["U"] = U
+        mats, ns, rows, cols, collide = S.batch_patterns(U, 4096, 8, 24, 1)
+        scale = [1.0 / float(np.prod([math.factorial(int(x)) for x in np.bincount(c)])) for c in cols]
+        bp = B.BatchedPermanents(mats, method="glynn", scale=scale)
+        tuned = bp.autotune(candidates=[(9, 128), (11, 64), (11, 128), (13, 128)], reps=1)
+        bp.capture()
+        bp.replay()
+        t = timed(bp.replay, reps=3)
+        terms = int(sum(2 ** (int(n) - 1) for n in ns))
+        # sampled parity of the batched kernel: the 8 stored items (n <= 14) of this batch, with their oracle values
+        items = refs["batched_items"]
+        pick = [unflat(r["matrix"], r["n"], r["n"]) for r in items]
+
+        def sampled_err(prec):
+            per8, _ = pg.batched(pick, method="glynn", prec=prec)
+            per8 = per8.cpu().numpy()
+            return max(ref_rel_err(r, pick[i], complex(per8[i])) for i, r in enumerate(items))
+
+        forms["batched_4096_n8-24"] = {"terms_per_s": terms / t, "perms_per_s": len(mats) / t, "s_per_replay": t,
+                                       "vs_plain_glynn": terms / t / ctx["base"],
+                                       "collision_items": int(collide.sum()),
+                                       "tuned": {"unit_log2": tuned["unit_log2"], "block": tuned["block"]},
+                                       "max_rel_err_sampled_vs_oracle": sampled_err("fp64")}
+        # the same batch in R3 (FP64 row sums, double-float products) and R4 (double-float walk)
+        for prec in ("fp64_df", "fp32x2"):
+            bpx = B.BatchedPermanents(mats, method="glynn", scale=scale, prec=prec, unit_log2=tuned["unit_log2"],
+                                      block=tuned["block"])
+            bpx.capture()
+            bpx.replay()
+            tx = timed(bpx.replay, reps=3)
+            forms["batched_4096_n8-24_" + prec] = {"terms_per_s": terms / tx, "perms_per_s": len(mats) / tx,
+                                                  "s_per_replay": tx, "vs_fp64_batch": t / tx,
+                                                  "max_rel_err_sampled_vs_oracle": sampled_err(prec)}
+
+    def adjoint():
+        # batch of 64 Gaussian matrices at n = 24
+        G = torch.as_tensor(np.stack([S.gaussian(24, b) for b in range(64)])).to(dev)
+        pg.grad(G[:1])
+        tg = timed(lambda: pg.grad(G))
+        tf = timed(lambda: [pg.glynn(G[b]) for b in range(64)])
+        _, _, M, _ = pg.grad(G[:1])
+        A0 = G[0].cpu().numpy()
+        P0 = complex(pg.glynn(G[0]).cpu().item())
+        lap = float(np.max(np.abs(np.sum(A0 * M[0].cpu().numpy(), axis=1) - P0)) / abs(P0))
+        forms["adjoint_64_n24"] = {"terms_per_s": 64 * 2 ** 23 / tg, "s": tg, "cost_vs_plain_same_batch": tg / tf,
+                                   "laplace_identity_rel_err": lap}
+        # n = 32 on a batch of 2 (items run one after another: per-item rate as for 64)
+        G32 = torch.as_tensor(np.stack([S.gaussian(32, b) for b in range(2)])).to(dev)
+        tg32 = timed(lambda: pg.grad(G32))
+        tf32 = timed(lambda: [pg.glynn(G32[b]) for b in range(2)])
+        forms["adjoint_2_n32"] = {"terms_per_s": 2 * 2 ** 31 / tg32, "s": tg32,
+                                  "cost_vs_plain_same_batch": tg32 / tf32}
+
+    def collisions():
+        # n = 28: the multiplicity expansion against the plain kernel on the expanded matrix
+        coll = {}
+        for mult in ([2, 1, 1, 1], [2, 2, 2, 1], [3, 2, 2, 2, 2, 1]):
+            mult = mult + [1] * (28 - sum(mult))
+            Bh = S.circular_gaussian((28, len(mult)), 2800 + len(mult), 1.0 / 28)
+            dB = torch.as_tensor(Bh).to(dev)
+            dE = torch.as_tensor(np.ascontiguousarray(np.repeat(Bh, mult, axis=1))).to(dev)
+            pg.glynn_mult(dB, mult)
+            tm = timed(lambda: pg.glynn_mult(dB, mult), reps=2)
+            tp = timed(lambda: pg.glynn(dE), reps=2)
+            a, b = complex(pg.glynn_mult(dB, mult).cpu().item()), complex(pg.glynn(dE).cpu().item())
+            key = "+".join(str(m) for m in mult if m > 1)
+            coll[key] = {"s": tm, "speedup_vs_expanded": tp / tm, "rel_diff_vs_expanded": abs(a - b) / abs(b)}
+        forms["collisions_n28"] = coll
+
+    def minors():
+        # row minors of a 31 x 32 matrix in one pass, against the forward kernel at n = 32
+        M32 = torch.as_tensor(S.circular_gaussian((31, 32), 0, 1.0 / 32)).to(dev)
+        for rp in ("fp64", "fp64_df", "fp32x2"):
+            pg.row_minors(M32, prec=rp)
+            tmr = timed(lambda: pg.row_minors(M32, prec=rp))
+            key = "row_minors_k32" + ("" if rp == "fp64" else "_" + rp)
+            forms[key] = {"terms_per_s": 2 ** 31 / tmr, "s": tmr, "cost_vs_glynn_n32": tmr * ctx["base"] / 2 ** 31}
+
+    def sampler():
+        # 16 draws of 24 photons in the 1000-mode unitary (one graph replay per batch)
+        U = ctx["U"] if "U" in ctx else S.haar_unitary(1000, 0)
+        n, ns = 24, 16
+        A24 = torch.as_tensor(S.gaussian(24, 0)).to(dev)
+        pg.glynn(A24)
+        t24 = timed(lambda: pg.glynn(A24), reps=2)
+        # sampled parity: 4 draws of 8 photons in 30 modes against the oracle's stored draws
+        rs = refs["sampler_m30_n8"]
+        U30 = unflat(rs["U"], 30, 30)
+        for rp in ("fp64", "fp64_df", "fp32x2"):
+            smp, _, _ = sampler_case(pg, U, n, ns, 5, dev, prec=rp)
+            smp.capture()
+            smp.replay()
+            ts = timed(smp.replay, reps=2)
+            s30, _, _ = sampler_case(pg, U30, 8, 4, 6, dev, prec=rp)
+            got = s30.run().cpu().numpy()
+            same = "%d/4" % sum(int(list(got[i]) == rs["draws"][i]) for i in range(4))
+            key = "boson_sample_m1000_n24_x16" + ("" if rp == "fp64" else "_" + rp)
+            forms[key] = {"draws_per_s": ns / ts, "s_per_replay": ts, "terms_per_s": ns * (2 ** n - 2) / ts,
+                          "cost_per_draw_in_glynn_n24": ts / ns / t24, "launches_per_replay": 2 * n - 1,
+                          "draws_equal_oracle_m30_n8": same}
+
+    for name, fn in (("glynn_n32", ladder), ("batched_4096_n8-24", batched), ("adjoint", adjoint),
+                     ("collisions_n28", collisions), ("row_minors_k32", minors),
+                     ("boson_sample_m1000_n24_x16", sampler)):
+        try:
+            fn()
+        except Exception as e:  # one form failing must not take the bench line down
+            forms[name + "_error"] = "%s: %s" % (type(e).__name__, e)
     return forms
 
 
