@@ -14,8 +14,10 @@
  *   perm_c128 layout-compatible with C99 double _Complex / torch.complex128.
  * - Every pointer named d* is DEVICE memory owned by the caller; the library
  *   allocates no device memory.  Entry points that need scratch take a caller
- *   workspace (query its size with the matching *_workspace function); pass a
- *   16-byte-aligned buffer of at least that size.  The library never frees it.
+ *   workspace (query its size with the matching *_workspace_size function);
+ *   pass a 256-byte-aligned buffer of at least that size (perm_glynn, perm_ryser
+ *   and the range calls accept 16-byte alignment).  The library never frees it.
+ *   (perm_glynn_noalloc instead uses a fixed array compiled into the library.)
  * - Calls are asynchronous and stream-ordered on `stream` (a cudaStream_t;
  *   NULL = the legacy default stream), except prob_sample which synchronises
  *   the stream and returns a host value.  Two calls that share a workspace must
