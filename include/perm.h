@@ -15,8 +15,9 @@
  * - Every pointer named d* is DEVICE memory owned by the caller; the library
  *   allocates no device memory.  Entry points that need scratch take a caller
  *   workspace (query its size with the matching *_workspace_size function);
- *   pass a 256-byte-aligned buffer of at least that size (perm_glynn, perm_ryser
- *   and the range calls accept 16-byte alignment).  The library never frees it.
+ *   pass a 256-byte-aligned buffer of at least that size (perm_glynn,
+ *   perm_ryser, perm_ryser_nw, the range calls and perm_glynn_mult accept
+ *   16-byte alignment).  The library never frees it.
  *   (perm_glynn_noalloc instead uses a fixed array compiled into the library.)
  * - Calls are asynchronous and stream-ordered on `stream` (a cudaStream_t;
  *   NULL = the legacy default stream), except prob_sample which synchronises
