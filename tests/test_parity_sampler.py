@@ -206,3 +206,30 @@ def test_graph_replay_matches_run(pg):
     smp.load(dev(alpha2), dev(u2))
     third = smp.replay().cpu().numpy()
     check_against_oracle(S.haar_unitary(m, 12), list(range(0, 2 * n, 2)), alpha2, u2, third)
+
+
+@pytest.mark.parametrize("m,n,ns", [(5, 1, 30), (6, 6, 12), (2, 2, 40)])
+def test_draw_edge_sizes_match_oracle(pg, m, n, ns):
+    """One photon (weights |U[in, l]|^2 only), every mode occupied (m = n), the
+    smallest interferometer: equal draws to the oracle's."""
+    U = S.haar_unitary(m, 50 + m + n)
+    inputs = list(range(m - n, m))
+    alpha, u = draws(60 + m + n, ns, n)
+    got = pg.boson_sample(dev(U), inputs, dev(alpha), dev(u)).cpu().numpy()
+    check_against_oracle(U, inputs, alpha, u, got)
+    assert (got >= 0).all() and (got < m).all()
+
+
+def test_identity_photon_order_and_row_minors_batch_of_one(pg):
+    """alpha = identity for every draw is valid; a batch of one matrix equals the unbatched call."""
+    import numpy as np_
+    m, n, ns = 12, 5, 6
+    U = S.haar_unitary(m, 77)
+    alpha = np_.tile(np_.arange(n, dtype=np_.int32), (ns, 1))
+    _, u = draws(78, ns, n)
+    got = pg.boson_sample(dev(U), [1, 3, 5, 7, 9], dev(alpha), dev(u)).cpu().numpy()
+    check_against_oracle(U, [1, 3, 5, 7, 9], alpha, u, got)
+    M = S.circular_gaussian((8, 9), 79, 1.0 / 9)
+    one = pg.row_minors(dev(M)).cpu().numpy()
+    batch = pg.row_minors(dev(M[None, :, :])).cpu().numpy()
+    assert np_.array_equal(one, batch[0])
