@@ -14,7 +14,9 @@ Ryser: x (-1)^n) — the paper's Algorithms 1/2 split of the iteration range,
 with the final reduce done from the logs.
 
 Each log line carries a hash of the matrix, the method and the chunking, so a
-log from another problem is rejected instead of mixed in.
+log from another problem is rejected instead of mixed in.  A line torn by an
+interrupted write is skipped (its chunk counts as missing) and the next record
+starts on a new line.
 """
 from __future__ import annotations
 
@@ -58,7 +60,7 @@ def read_log(path: str, key: str) -> dict:
             try:
                 rec = json.loads(line)
             except ValueError:
-                break  # a torn last line from an interrupted write
+                continue  # a torn line from an interrupted write: its chunk is recomputed
             if rec.get("key") != key:
                 raise ValueError("log %s belongs to another problem" % path)
             done[int(rec["chunk"])] = (complex(*rec["hi"]), complex(*rec["lo"]))
@@ -67,8 +69,15 @@ def read_log(path: str, key: str) -> dict:
 
 def append_log(path: str, key: str, chunk: int, kb: int, ke: int, hi: complex, lo: complex):
     rec = {"key": key, "chunk": chunk, "k_begin": kb, "k_end": ke, "hi": [hi.real, hi.imag], "lo": [lo.real, lo.imag]}
+    # After an interrupted write the file ends inside a record: start on a fresh
+    # line so that the new record stays parsable.
+    torn = False
+    if os.path.exists(path) and os.path.getsize(path) > 0:
+        with open(path, "rb") as f:
+            f.seek(-1, os.SEEK_END)
+            torn = f.read(1) != b"\n"
     with open(path, "a") as f:
-        f.write(json.dumps(rec) + "\n")
+        f.write(("\n" if torn else "") + json.dumps(rec) + "\n")
         f.flush()
         os.fsync(f.fileno())
 

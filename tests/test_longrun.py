@@ -46,6 +46,34 @@ def test_two_ranks_and_torn_line(tmp_path):
     assert oracle.ryser(A).rel_err(per) < 1e-13
 
 
+@pytest.mark.parametrize("method", ["glynn", "ryser"])
+def test_resume_after_torn_write(tmp_path, method):
+    """An interrupted run leaves a torn record at the end of its log; the resumed
+    run recomputes only that chunk and the ones never started, appends parsable
+    records after the fragment, and the combined result matches the oracle."""
+    A = S.gaussian(11, 8)
+    log = str(tmp_path / "run.jsonl")
+    calls = []
+
+    def fn(kb, ke):
+        calls.append((kb, ke))
+        return oracle_partial(A, method)(kb, ke)
+
+    total = longrun.n_chunks(11, method, 6)
+    assert longrun.run(A, log, fn, method=method, chunk_log2=6, max_chunks=3) == 3
+    with open(log) as f:
+        lines = f.read().splitlines()
+    # the third record was cut short by the interruption
+    with open(log, "w") as f:
+        f.write("\n".join(lines[:2]) + "\n" + lines[2][:25])
+    calls.clear()
+    assert longrun.run(A, log, fn, method=method, chunk_log2=6) == total - 2
+    assert len(calls) == len(set(calls)) == total - 2  # no chunk computed twice
+    assert longrun.run(A, log, fn, method=method, chunk_log2=6) == 0
+    per = longrun.combine(A, [log], method=method, chunk_log2=6)
+    assert per is not None and oracle.ryser(A).rel_err(per) < 1e-13
+
+
 def test_log_of_another_problem_is_rejected(tmp_path):
     A, B = S.gaussian(9, 5), S.gaussian(9, 6)
     log = str(tmp_path / "run.jsonl")
