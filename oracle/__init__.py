@@ -18,6 +18,13 @@ evaluates, and which passage of arXiv 1606.05836 it follows:
 * :func:`ryser_range`,
   :func:`glynn_range`   -- partial sums of the un-normalised terms over an index
                            range, binary or reflected-Gray index-to-set mapping.
+* :func:`glynn_f64dd`,
+  :func:`glynn_f64dd_range`,
+  :func:`ryser_f64dd_range` -- Eq. (S2) / (S1) in reflected-Gray order in FP64
+                           (row sums, updates, products) with every term added to
+                           a double-double accumulator; pieces of 2^6 indices
+                           start from row sums computed from scratch.  The
+                           oracle for n = 29-40, where quad precision is too slow.
 * :func:`ryser_int`     -- Eq. (S1) exactly, integers modulo 2^128.
 * :func:`minors`        -- Per of every (n-1)x(n-1) minor = dPer/da_ij.
 * :func:`prob`          -- Eq. (1), |Per(U_ST)|^2 / (prod s_i! prod t_j!).
@@ -45,7 +52,9 @@ def build(force: bool = False) -> str:
     """Compile oracle.c into liboracle.so with gcc (OpenMP).  Returns the path."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu11", "-o", tmp, _SRC]
+        # no contraction of a*b+c into FMAs: the same rounding on every host
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-std=gnu11", "-o", tmp, _SRC,
+               "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -64,13 +73,17 @@ def _load():
         lib.oracle_glynn_gray.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp]
         lib.oracle_ryser_range.argtypes = [ctypes.c_int, dp, u64, u64, ctypes.c_int, ctypes.c_int, dp]
         lib.oracle_glynn_range.argtypes = [ctypes.c_int, dp, u64, u64, ctypes.c_int, ctypes.c_int, dp]
+        lib.oracle_glynn_f64dd.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp]
+        lib.oracle_glynn_f64dd_range.argtypes = [ctypes.c_int, dp, u64, u64, ctypes.c_int, dp]
+        lib.oracle_ryser_f64dd_range.argtypes = [ctypes.c_int, dp, u64, u64, ctypes.c_int, dp]
         lib.oracle_ryser_z128.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_uint64)]
         lib.oracle_minors.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp]
         lib.oracle_prob.argtypes = [ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int32),
                                     ctypes.POINTER(ctypes.c_int32), ctypes.c_int, dp, dp]
         for f in ("oracle_perm_def", "oracle_ryser", "oracle_glynn", "oracle_glynn_gray", "oracle_ryser_range",
-                  "oracle_glynn_range", "oracle_ryser_z128", "oracle_minors", "oracle_prob"):
+                  "oracle_glynn_range", "oracle_ryser_z128", "oracle_minors", "oracle_prob", "oracle_glynn_f64dd",
+                  "oracle_glynn_f64dd_range", "oracle_ryser_f64dd_range"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -166,6 +179,32 @@ def glynn_range(A, k_begin: int, k_end: int, gray: bool = True, threads: int = 0
     out = np.zeros(4)
     _check(_load().oracle_glynn_range(A.shape[0], _dp(A), int(k_begin), int(k_end), int(bool(gray)),
                                       threads, _dp(out)), "glynn_range")
+    return _qc(out)
+
+
+def glynn_f64dd(A, threads: int = 0) -> QC:
+    """Per(A) by Eq. (S2) in Gray order: FP64 terms, double-double sum, n <= 48."""
+    A = _as_c128(A)
+    out = np.zeros(4)
+    _check(_load().oracle_glynn_f64dd(A.shape[0], _dp(A), threads, _dp(out)), "glynn_f64dd")
+    return _qc(out)
+
+
+def glynn_f64dd_range(A, k_begin: int, k_end: int, threads: int = 0) -> QC:
+    """FP64 / double-double Glynn partial sum over Gray indices [k_begin, k_end), no 1/2^{n-1}."""
+    A = _as_c128(A)
+    out = np.zeros(4)
+    _check(_load().oracle_glynn_f64dd_range(A.shape[0], _dp(A), int(k_begin), int(k_end), threads, _dp(out)),
+           "glynn_f64dd_range")
+    return _qc(out)
+
+
+def ryser_f64dd_range(A, k_begin: int, k_end: int, threads: int = 0) -> QC:
+    """FP64 / double-double Ryser partial sum over Gray indices [k_begin, k_end), no (-1)^n."""
+    A = _as_c128(A)
+    out = np.zeros(4)
+    _check(_load().oracle_ryser_f64dd_range(A.shape[0], _dp(A), int(k_begin), int(k_end), threads, _dp(out)),
+           "ryser_f64dd_range")
     return _qc(out)
 
 

@@ -364,3 +364,154 @@ def test_glynn_gray_pins():
     # exact integer counts of 0/1 matrices
     C = S.bernoulli01(16, 9)
     assert oracle.glynn_gray(C.astype(np.complex128)).hi == oracle.ryser_int(C)
+
+
+# --------------------------------------------------------------------------
+# FP64 Gray-order sums with double-double accumulation (the oracle for n = 29-40)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 12, 17, 20])
+def test_f64dd_glynn_against_quad(n):
+    """FP64 terms + double-double sum agree with the quad Gray-order evaluation to
+    FP64 rounding (the products' relative error, ~n eps, is all that is left)."""
+    A = S.gaussian(n, 50 + n)
+    q = oracle.glynn_gray(A)
+    assert qrel(q, oracle.glynn_f64dd(A)) < 1e-13
+    # any thread split gives the same value to double-double rounding
+    assert qrel(oracle.glynn_f64dd(A, threads=1), oracle.glynn_f64dd(A, threads=5)) < 1e-28
+
+
+@pytest.mark.parametrize("n", [2, 5, 12, 17, 20])
+def test_f64dd_ryser_against_quad(n):
+    """Ryser in FP64 loses digits to cancellation (the paper's finding), but its
+    Gray-order FP64 sum still tracks the quad value at these sizes."""
+    A = S.gaussian(n, 60 + n)
+    q = oracle.ryser_range(A, 0, 1 << n, gray=True)
+    f = oracle.ryser_f64dd_range(A, 0, 1 << n)
+    assert abs((f.hi - q.hi) + (f.lo - q.lo)) <= 1e-9 * abs(q.hi)
+
+
+def test_f64dd_exact_on_small_integers():
+    """0/1 and other small-integer matrices at n = 12: every row sum, product and
+    partial sum is an integer below 2^53, so both FP64 sums are exact."""
+    for seed in range(4):
+        B = S.bernoulli01(12, seed)
+        want = oracle.ryser_int(B)
+        Bc = B.astype(np.complex128)
+        g = oracle.glynn_f64dd(Bc)
+        assert g.hi == want and g.lo == 0
+        r = oracle.ryser_f64dd_range(Bc, 0, 1 << 12)
+        assert r.hi == want and r.lo == 0  # (-1)^12 = 1
+    ex = {r["name"]: r for r in read_tsv("worked_examples.tsv")}
+    assert oracle.glynn_f64dd(S.all_r(12, 1.0)).hi == float(ex["ones"]["value_re"])
+    assert oracle.glynn_f64dd(S.ones_minus_identity(12)).hi == float(ex["ones_minus_identity"]["value_re"])
+    d = [1, 0]  # derangement numbers, D(n) = (n - 1)(D(n-1) + D(n-2))
+    for k in range(2, 12):
+        d.append((k - 1) * (d[-1] + d[-2]))
+    r = oracle.ryser_f64dd_range(S.ones_minus_identity(11), 0, 1 << 11)
+    assert -r.hi == d[11]  # (-1)^11 is outside the range sum
+
+
+def test_f64dd_paper_diag_1pi_n45_range():
+    """The paper's 45 x 45 diag(1+i) run: every Glynn term is (1+i)^45, exactly
+    representable, so a range sum is the count times (1+i)^45 with no rounding;
+    the range straddles the top of the 2^44 index space and crosses piece starts."""
+    n = 45
+    A = S.diagonal([1 + 1j] * n)
+    w = (1 + 1j) ** 45
+    for kb, ke in [(0, 1000), ((1 << 44) - 12345, 1 << 44), (777, 777), (63, 65)]:
+        got = oracle.glynn_f64dd_range(A, kb, ke, threads=3)
+        assert got.hi == (ke - kb) * w and got.lo == 0
+
+
+def test_f64dd_range_additivity_across_pieces():
+    """Cutting the range at arbitrary points (inside pieces, at piece starts, empty
+    pieces) gives the same total to double-double rounding: a piece boundary
+    restarts the row sums but changes no term."""
+    A = S.gaussian(15, 77, 1.0)
+    total = 1 << 14
+    full = oracle.glynn_f64dd_range(A, 0, total, threads=2)
+    cuts = [0, 1, 63, 64, 65, 1000, 4096, 4097, 9999, total]
+    parts = [oracle.glynn_f64dd_range(A, a, b, threads=2) for a, b in zip(cuts[:-1], cuts[1:])]
+    s = sum((p.hi for p in parts), 0j) + sum((p.lo for p in parts), 0j)
+    scale = float(np.sum(np.abs([p.hi for p in parts])))
+    assert abs(s - full.hi - full.lo) <= 1e-15 * scale
+    # and the full Glynn range over 2^(n-1) matches the normalised permanent
+    assert qrel(oracle.glynn(A), oracle.glynn_f64dd(A)) < 1e-13
+    R = oracle.ryser_f64dd_range(A, 0, 1 << 15, threads=2)
+    rparts = [oracle.ryser_f64dd_range(A, a, b, threads=2) for a, b in [(0, 5), (5, 6000), (6000, 1 << 15)]]
+    rs = sum((p.hi + p.lo for p in rparts), 0j)
+    assert abs(rs - (R.hi + R.lo)) <= 1e-15 * float(np.sum(np.abs([p.hi for p in rparts])))
+
+
+def test_f64dd_closed_forms_n24():
+    """Rank-one u v^T (n! prod u prod v), a permuted block-diagonal matrix (product of
+    the blocks' quad permanents) and the paper's all-r values at n = 24."""
+    A, u, v = S.rank_one(24, 601)
+    want = math.factorial(24) * np.prod(u) * np.prod(v)
+    assert abs(oracle.glynn_f64dd(A).hi - want) <= 1e-11 * abs(want)
+    B1, B2 = S.gaussian(12, 911), S.gaussian(12, 912)
+    Z = np.zeros((24, 24), dtype=np.complex128)
+    Z[:12, :12], Z[12:, 12:] = B1, B2
+    P, Q = S.random_permutations(24, 913)
+    want = oracle.glynn(B1).hi * oracle.ryser(B2).hi
+    assert oracle.glynn_f64dd(Z[P][:, Q]).rel_err(want) < 1e-13
+    assert oracle.glynn_f64dd(S.all_r(24, 1 + 1j)).rel_err(closed_allr(24, 1 + 1j)) < 1e-13
+
+
+def test_f64dd_allones_precision_within_paper_band():
+    """FP64 BB/FG on all-ones (the paper's precision tables): the error against n!
+    stays at or below the printed BB/FG errors (double-double accumulation only
+    removes the summation part of the paper's error)."""
+    paper = {int(r["n"]): float(r["bbfg_relerr"]) for r in read_tsv("precision_allones.tsv")}
+    for n in (20, 24, 26):
+        g = oracle.glynn_f64dd(S.all_r(n, 1.0))
+        exact = math.factorial(n)
+        err = abs(Fraction(g.hi.real) + Fraction(g.lo.real) - exact) / exact
+        assert float(err) <= 10 * paper[n] + 1e-15, (n, float(err), paper[n])
+
+
+def test_f64dd_ones_noise_against_stored_quad():
+    """The heavy-cancellation input of the precision ladder (all-ones + 1e-3
+    Gaussian) at n = 24 against its stored quad Gray-order value."""
+    row = [r for r in read_tsv("ladder_refs.tsv") if r["kind"] == "ones_noise" and int(r["n"]) == 24][0]
+    A = S.ones_plus_noise(24, 0)
+    f = oracle.glynn_f64dd(A)
+    hi = complex(float(row["re_hi"]), float(row["im_hi"]))
+    lo = complex(float(row["re_lo"]), float(row["im_lo"]))
+    assert abs((f.hi - hi) + (f.lo - lo)) <= 1e-11 * abs(hi)
+
+
+def _large_ref(kind, n, seed):
+    rows = [r for r in read_tsv("large_refs.tsv") if r["kind"] == kind and int(r["n"]) == n and int(r["seed"]) == seed]
+    assert rows, "no stored reference for %s n=%d seed=%d (tests/golden/make_large_refs.py)" % (kind, n, seed)
+    r = rows[0]
+    return r["sha"], complex(float(r["re_hi"]) + float(r["re_lo"]), float(r["im_hi"]) + float(r["im_lo"]))
+
+
+def test_f64dd_against_quad_at_n32_stored():
+    """At n = 32 the quad oracle takes ~50 min per matrix, so its values of the
+    benchmark's Gaussian inputs are stored (make_sweep_refs.py); the FP64 /
+    double-double evaluations of the same inputs (make_large_refs.py) agree with
+    them far inside the 1e-10 bar."""
+    quad = {int(r["seed"]): r for r in read_tsv("sweep_refs.tsv") if r["oracle"] == "glynn_gray" and r["n"] == "32"}
+    assert sorted(quad) == [0, 1, 2]
+    for seed, q in quad.items():
+        sha, fv = _large_ref("gaussian", 32, seed)
+        assert q["sha"] == sha
+        qv = complex(float(q["re_hi"]) + float(q["re_lo"]), float(q["im_hi"]) + float(q["im_lo"]))
+        assert abs(qv - fv) <= 1e-12 * abs(qv), seed
+
+
+@pytest.mark.slow
+def test_f64dd_n32_recomputed_against_stored_quad():
+    """One full n = 32 evaluation (2^31 FP64 terms, ~40 s on 8 cores) of the
+    benchmark's seed-0 input against its stored quad value."""
+    import hashlib
+    row = [r for r in read_tsv("sweep_refs.tsv") if r["oracle"] == "glynn_gray" and r["n"] == "32" and r["seed"] == "0"]
+    A = S.gaussian(32, 0)
+    assert hashlib.sha256(np.ascontiguousarray(A).tobytes()).hexdigest()[:16] == row[0]["sha"]
+    f = oracle.glynn_f64dd(A)
+    q = row[0]
+    qv = complex(float(q["re_hi"]) + float(q["re_lo"]), float(q["im_hi"]) + float(q["im_lo"]))
+    assert abs((f.hi + f.lo) - qv) <= 1e-12 * abs(qv)
