@@ -120,6 +120,21 @@ int perm_glynn_range(const perm_c128* dA, int n, int lda, uint64_t k_begin, uint
 int perm_ryser_range(const perm_c128* dA, int n, int lda, uint64_t k_begin, uint64_t k_end, perm_c128* dOut,
                      void* dWork, size_t workBytes, const perm_opts* opts, void* stream);
 
+/* Per(A) from partial sums over disjoint Gray-index ranges that together cover
+ * [0, 2^M): the final reduce of Algorithms 1 and 2 (there an MPI reduce of the
+ * per-process sums, followed by the formula's normalisation), for partials
+ * computed by perm_glynn_range / perm_ryser_range on several GPUs or boxes, or
+ * chunk by chunk in a checkpointed run.
+ * hParts: host, [count][2] perm_c128: partial p as the (hi, lo) pair the range
+ *         call wrote.  They are added in double-double in the order p = 0 ..
+ *         count-1 (pass them in range order for a result that does not depend
+ *         on how the work was spread).
+ * method: 0 = Glynn (the sum times 2^-(n-1), exact), 1 = Ryser (times (-1)^n).
+ * hOut:   host, [2] perm_c128: Per(A) as (hi, lo).
+ * Host arithmetic only (no device, no stream).  1 <= n <= PERM_MAX_N,
+ * count >= 1; non-finite partials give a non-finite result. */
+int perm_combine_partials(const perm_c128* hParts, int count, int n, int method, perm_c128* hOut);
+
 /* --- batched permanents --------------------------------------------------- */
 
 /* Many permanents of mixed sizes 1 <= n_i <= PERM_BATCH_MAX_N in one persistent,
@@ -289,6 +304,18 @@ int boson_sample(const perm_c128* dU, int m, int ldu, int n, const int32_t* hInp
                  const perm_opts* opts, void* stream);
 
 /* --- diagnostics ----------------------------------------------------------- */
+
+/* FP64 FMA throughput probe: grid x block threads each run
+ * PERM_FP64_PROBE_CHAINS independent dependent chains of `iters` fused
+ * multiply-adds (x <- x a + b), i.e. grid x block x iters x
+ * PERM_FP64_PROBE_CHAINS DFMA instructions, 2 FP64 flops each.  Time it with
+ * events on `stream` to measure the FP64 peak against which the permanent
+ * kernels' FLOP rates are reported (they are bound by the FP64 pipe).  dSink:
+ * one device double that the kernel never actually writes (it keeps the chains
+ * live).  iters >= 1, grid >= 1, block a multiple of 32 in 32..1024.
+ * Asynchronous. */
+#define PERM_FP64_PROBE_CHAINS 4
+int perm_fp64_fma_probe(int iters, int grid, int block, double* dSink, void* stream);
 
 const char* perm_strerror(int status);
 /* The cudaError_t of the most recent PERM_ECUDA on this host thread (0 if none). */

@@ -12,6 +12,8 @@ Functions mirror the C entry points:
 * :func:`ryser_nw` -- Per(A), Ryser's formula halved to 2^(n-1) subsets
 * :func:`glynn_mult` -- Per with repeated columns (photon collisions), multiplicity expansion
 * :func:`glynn_range`, :func:`ryser_range` -- partial sums over a Gray-index range
+* :func:`combine_partials` -- Per(A) from such partials (the final reduce of
+  Algorithms 1/2 and the normalisation), host arithmetic in the C library
 * :func:`batched`, :class:`BatchedPermanents` -- many permanents of mixed sizes in
   one persistent launch (CUDA-graph capture, autotuned launch shape)
 * :func:`prob` -- Eq. (1): |Per(U_ST)|^2 / (prod s_i! prod t_j!) for one (S, T)
@@ -31,7 +33,8 @@ from . import _native
 from ._native import PERM_MAX_N, PRECISIONS, Opts, PermError
 from ._workspace import workspace as _workspace
 
-__all__ = ["glynn", "glynn_mult", "ryser", "ryser_nw", "glynn_range", "ryser_range", "workspace_size", "PermError",
+__all__ = ["glynn", "glynn_mult", "ryser", "ryser_nw", "glynn_range", "ryser_range", "combine_partials",
+           "fp64_fma_probe", "workspace_size", "PermError",
            "PERM_MAX_N", "PRECISIONS", "library", "batched", "BatchedPermanents", "grad", "PermAbs2", "prob",
            "row_minors", "BosonSampler", "boson_sample"]
 
@@ -178,6 +181,36 @@ def glynn_range(A, k_begin: int, k_end: int, prec="fp64", chunk_log2=0, block=0,
 def ryser_range(A, k_begin: int, k_end: int, prec="fp64", chunk_log2=0, block=0, grid=0) -> torch.Tensor:
     """Un-normalised Ryser partial sum over Gray indices [k_begin, k_end): tensor (hi, lo)."""
     return _range("perm_ryser_range", A, k_begin, k_end, prec=prec, chunk_log2=chunk_log2, block=block, grid=grid)
+
+
+def combine_partials(parts, n: int, method: str = "glynn") -> tuple[complex, complex]:
+    """Per(A) as (hi, lo) from (hi, lo) partial sums over disjoint Gray ranges that
+    cover the whole index space, summed in the given order (``perm_combine_partials``;
+    host arithmetic, no device needed)."""
+    import numpy as np
+
+    if method not in ("glynn", "ryser"):
+        raise ValueError("method must be 'glynn' or 'ryser'")
+    buf = np.ascontiguousarray(np.asarray([[complex(h), complex(l)] for h, l in parts], dtype=np.complex128))
+    if buf.ndim != 2 or buf.shape[0] < 1:
+        raise ValueError("at least one (hi, lo) partial is needed")
+    out = np.zeros(2, dtype=np.complex128)
+    st = library().perm_combine_partials(ctypes.c_void_p(buf.ctypes.data), buf.shape[0], int(n),
+                                         0 if method == "glynn" else 1, ctypes.c_void_p(out.ctypes.data))
+    _native.check(st, "perm_combine_partials")
+    return complex(out[0]), complex(out[1])
+
+
+def fp64_fma_probe(iters: int, grid: int, block: int = 256, device=None) -> int:
+    """Launch the FP64 FMA throughput probe on the current stream of ``device``;
+    returns the number of DFMA instructions it issues (time it with CUDA events)."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    sink = _workspace(dev, 256)
+    with torch.cuda.device(dev):
+        st = library().perm_fp64_fma_probe(int(iters), int(grid), int(block), ctypes.c_void_p(sink.data_ptr()),
+                                           ctypes.c_void_p(_stream_ptr(dev)))
+    _native.check(st, "perm_fp64_fma_probe")
+    return int(iters) * int(grid) * int(block) * 4
 
 
 from .batch import BatchedPermanents, batched  # noqa: E402

@@ -24,6 +24,7 @@ EXPORTS = (
     "perm_ryser_nw",
     "perm_glynn_range",
     "perm_ryser_range",
+    "perm_combine_partials",
     "perm_batched_workspace_size",
     "perm_batched",
     "perm_glynn_mult_workspace_size",
@@ -37,6 +38,7 @@ EXPORTS = (
     "perm_row_minors",
     "boson_sample_workspace_size",
     "boson_sample",
+    "perm_fp64_fma_probe",
     "perm_strerror",
     "perm_last_cuda_error",
     "perm_version",
@@ -80,6 +82,10 @@ def load(path: str | None = None):
     for f in ("perm_glynn_range", "perm_ryser_range"):
         getattr(lib, f).argtypes = [vp, i32, i32, u64, u64, vp, vp, sz, op, vp]
         getattr(lib, f).restype = i32
+    lib.perm_combine_partials.argtypes = [vp, i32, i32, i32, vp]
+    lib.perm_combine_partials.restype = i32
+    lib.perm_fp64_fma_probe.argtypes = [i32, i32, i32, vp, vp]
+    lib.perm_fp64_fma_probe.restype = i32
     i32p = ctypes.POINTER(ctypes.c_int32)
     lib.perm_batched_workspace_size.argtypes = [i32, i32p, i32, op]
     lib.perm_batched_workspace_size.restype = sz

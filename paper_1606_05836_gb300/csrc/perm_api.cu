@@ -2,6 +2,7 @@
 // templated kernels.  The declarations and their contracts are in include/perm.h.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <math.h>
 #include <stdlib.h>
 
 #include <mutex>
@@ -131,6 +132,17 @@ int plan_fwd(int n, int kind, uint64_t range, const perm_opts* o, Plan* p) {
   p->per_q = range / P;
   p->per_r = range % P;
   return PERM_OK;
+}
+
+// (sh, sl) += (h, l) in double-double: Knuth's TwoSum of the high parts, the
+// low parts added to its error, then renormalised.
+void host_dd_add(double& sh, double& sl, double h, double l) {
+  const double s = sh + h;
+  const double bv = s - sh;
+  double e = (sh - (s - bv)) + (h - bv);
+  e += sl + l;
+  sh = s + e;
+  sl = e - (sh - s);
 }
 
 size_t workspace_for_grid(int grid) { return 256 + (size_t)grid * 4 * sizeof(double); }
@@ -367,6 +379,27 @@ int perm_ryser_range(const perm_c128* dA, int n, int lda, uint64_t k_begin, uint
 }
 
 
+int perm_combine_partials(const perm_c128* hParts, int count, int n, int method, perm_c128* hOut) {
+  if (!hParts || !hOut || count < 1 || (method != 0 && method != 1)) return PERM_EINVAL;
+  if (n < 1 || n > PERM_MAX_N) return PERM_ERANGE;
+  // double-double sum in the given order (TwoSum of the high parts, low parts
+  // added, renormalised), then the exact scaling of the formula
+  double rh = 0.0, rl = 0.0, ih = 0.0, il = 0.0;
+  for (int p = 0; p < count; p++) {
+    const perm_c128 hi = hParts[2 * p], lo = hParts[2 * p + 1];
+    host_dd_add(rh, rl, hi.re, lo.re);
+    host_dd_add(ih, il, hi.im, lo.im);
+  }
+  double f = 1.0;
+  int e = 0;
+  if (method == 0) e = -(n - 1);
+  else if (n & 1) f = -1.0;
+  hOut[0].re = ldexp(rh, e) * f;
+  hOut[0].im = ldexp(ih, e) * f;
+  hOut[1].re = ldexp(rl, e) * f;
+  hOut[1].im = ldexp(il, e) * f;
+  return PERM_OK;
+}
 
 size_t perm_glynn_mult_workspace_size(int n, int g, const int32_t* hMult, const perm_opts* opts) {
   if (!hMult || n < 1) return 0;

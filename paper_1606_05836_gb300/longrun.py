@@ -9,9 +9,9 @@ skips the chunks it already holds and continues; because each chunk's row sums
 are recomputed from scratch at its start, a chunk is re-runnable with no other
 state.  Ranks (processes or boxes) take disjoint chunk sets (chunk c belongs to
 rank c mod world) and write one log each; ``combine`` reads all logs and sums
-the partials in chunk order (deterministic), then scales (Glynn: / 2^(n-1);
-Ryser: x (-1)^n) — the paper's Algorithms 1/2 split of the iteration range,
-with the final reduce done from the logs.
+the partials in chunk order (deterministic) and scales them (Glynn: / 2^(n-1);
+Ryser: x (-1)^n) with ``perm_combine_partials`` — the paper's Algorithms 1/2
+split of the iteration range, with the final reduce done from the logs.
 
 Each log line carries a hash of the matrix, the method and the chunking, so a
 log from another problem is rejected instead of mixed in.  A line torn by an
@@ -26,7 +26,6 @@ import os
 
 import numpy as np
 
-from .shard import dd_sum
 
 
 def problem_key(A, method: str, chunk_log2: int, prec: str) -> str:
@@ -114,13 +113,10 @@ def combine(A, log_paths, method: str = "glynn", chunk_log2: int = 34, prec: str
     total = n_chunks(n, method, chunk_log2)
     if any(c not in done for c in range(total)):
         return None
-    parts = [done[c] for c in range(total)]
-    re = dd_sum((h.real, l.real) for h, l in parts)
-    im = dd_sum((h.imag, l.imag) for h, l in parts)
-    per = complex(re[0] + re[1], im[0] + im[1])
-    if method == "glynn":
-        return per / float(1 << (n - 1))
-    return -per if n & 1 else per
+    from . import combine_partials
+
+    hi, lo = combine_partials([done[c] for c in range(total)], n, method)
+    return hi + lo
 
 
 def gpu_run(A, log_path: str, method: str = "glynn", chunk_log2: int = 34, prec: str = "fp64", rank: int = 0,

@@ -7,8 +7,9 @@ takes one contiguous range of the iteration index, here of the Gray index
 Each rank computes its un-normalised double-double partial sum on its own GPU
 (``perm_glynn_range`` / ``perm_ryser_range``), and the one exchange of the method
 — the paper's final MPI reduce of the per-process sums — is an all-gather of the
-32-byte partials, summed in rank order on every rank (deterministic), then scaled
-(Glynn: / 2^(n-1); Ryser: x (-1)^n).
+32-byte partials; every rank then hands them, in rank order, to
+``perm_combine_partials`` (double-double sum and the formula's scaling, in the C
+library), so all ranks get the same value.
 
 A batch (the many output patterns of one interferometer) shards by item: every
 rank derives the same assignment from the item sizes alone (largest work first,
@@ -29,24 +30,8 @@ def shard_range(total: int, rank: int, world: int) -> tuple[int, int]:
     return begin, begin + q + (1 if rank < r else 0)
 
 
-def two_sum(a: float, b: float) -> tuple[float, float]:
-    s = a + b
-    bb = s - a
-    return s, (a - (s - bb)) + (b - bb)
-
-
-def dd_sum(pairs) -> tuple[float, float]:
-    """Sum of (hi, lo) double-double values in the given order."""
-    hi, lo = 0.0, 0.0
-    for h, l in pairs:
-        s, e = two_sum(hi, h)
-        e += lo + l
-        hi, lo = two_sum(s, e)
-    return hi, lo
-
-
-def exchange_partials(part: tuple[complex, complex], group=None) -> tuple[complex, complex]:
-    """All-gather every rank's (hi, lo) complex partial and sum them in rank order."""
+def exchange_partials(part: tuple[complex, complex], group=None) -> list[tuple[complex, complex]]:
+    """All-gather every rank's (hi, lo) complex partial; returns them in rank order."""
     import torch.distributed as dist
 
     world = dist.get_world_size(group)
@@ -56,9 +41,7 @@ def exchange_partials(part: tuple[complex, complex], group=None) -> tuple[comple
     bufs = [torch.empty_like(mine) for _ in range(world)]
     dist.all_gather(bufs, mine, group=group)
     vals = [b.cpu().tolist() for b in bufs]
-    re = dd_sum((v[0], v[2]) for v in vals)
-    im = dd_sum((v[1], v[3]) for v in vals)
-    return complex(re[0], im[0]), complex(re[1], im[1])
+    return [(complex(v[0], v[1]), complex(v[2], v[3])) for v in vals]
 
 
 def sharded_permanent(n: int, method: str, partial_fn, rank: int, world: int, group=None) -> complex:
@@ -70,17 +53,14 @@ def sharded_permanent(n: int, method: str, partial_fn, rank: int, world: int, gr
     """
     if n == 0:
         return 1.0 + 0.0j
+    from . import combine_partials
+
     M = n - 1 if method == "glynn" else n
     kb, ke = shard_range(1 << M, rank, world)
     part = partial_fn(kb, ke)
-    if world > 1:
-        hi, lo = exchange_partials(part, group)
-    else:
-        hi, lo = part
-    total = complex(hi.real + lo.real, hi.imag + lo.imag)
-    if method == "glynn":
-        return total / float(1 << (n - 1))
-    return -total if n & 1 else total
+    parts = exchange_partials(part, group) if world > 1 else [part]
+    hi, lo = combine_partials(parts, n, method)
+    return hi + lo
 
 
 def gpu_partial_fn(A: torch.Tensor, method: str = "glynn", **opts):

@@ -10,7 +10,8 @@ import torch.multiprocessing as mp
 
 import oracle
 import synthetic as S
-from paper_1606_05836_gb300.shard import dd_sum, item_work, shard_items, shard_range, sharded_batched, sharded_permanent
+from paper_1606_05836_gb300 import combine_partials
+from paper_1606_05836_gb300.shard import item_work, shard_items, shard_range, sharded_batched, sharded_permanent
 
 
 def test_shard_range_partitions_exactly():
@@ -24,10 +25,32 @@ def test_shard_range_partitions_exactly():
             assert max(lens) - min(lens) <= 1
 
 
-def test_dd_sum_is_exact_for_cancelling_parts():
-    parts = [(1e16, 1.0), (-1e16, 0.5), (3.0, 0.0)]
-    hi, lo = dd_sum(parts)
-    assert hi + lo == 4.5
+def test_combine_partials_double_double_and_scaling():
+    """perm_combine_partials (host code of the C library): the partials cancel
+    exactly in double-double, Glynn scales by 2^-(n-1), Ryser by (-1)^n, and it
+    matches the oracle's full sum when handed the oracle's range partials."""
+    parts = [(1e16 + 0j, 1.0 + 0j), (-1e16 + 2j, 0.5 + 0j), (3.0 + 0j, 0j)]
+    hi, lo = combine_partials(parts, 1, "glynn")
+    assert hi + lo == 4.5 + 2j
+    hi, lo = combine_partials(parts, 4, "glynn")
+    assert hi + lo == (4.5 + 2j) / 8
+    hi, lo = combine_partials(parts, 3, "ryser")
+    assert hi + lo == -(4.5 + 2j)
+    A = S.gaussian(13, 5)
+    cuts = [0, 17, 1000, 4095, 1 << 12]
+    g = [oracle.glynn_range(A, a, b, gray=True) for a, b in zip(cuts[:-1], cuts[1:])]
+    hi, lo = combine_partials([(p.hi, p.lo) for p in g], 13, "glynn")
+    assert oracle.glynn(A).rel_err(hi + lo) < 1e-15
+    cuts = [0, 5, 3000, 1 << 13]
+    r = [oracle.ryser_range(A, a, b, gray=True) for a, b in zip(cuts[:-1], cuts[1:])]
+    hi, lo = combine_partials([(p.hi, p.lo) for p in r], 13, "ryser")
+    assert oracle.ryser(A).rel_err(hi + lo) < 1e-15
+    import pytest as _pt
+    from paper_1606_05836_gb300 import PermError
+    with _pt.raises(PermError):
+        combine_partials(parts, 0, "glynn")
+    with _pt.raises(PermError):
+        combine_partials(parts, 49, "ryser")
 
 
 def _free_port():
@@ -87,10 +110,8 @@ def test_logical_shards_on_one_gpu():
     fn = gpu_partial_fn(dA, "glynn")
     K = 5
     parts = [fn(*shard_range(1 << 25, r, K)) for r in range(K)]
-    re = dd_sum((p[0].real, p[1].real) for p in parts)
-    im = dd_sum((p[0].imag, p[1].imag) for p in parts)
-    per = complex(re[0] + re[1], im[0] + im[1]) / float(1 << 25)
-    assert abs(per - full) <= 1e-12 * abs(full)
+    hi, lo = combine_partials(parts, 26, "glynn")
+    assert abs((hi + lo) - full) <= 1e-12 * abs(full)
     assert abs(sharded_permanent(26, "glynn", fn, 0, 1) - full) <= 1e-12 * abs(full)
 
 
