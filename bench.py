@@ -10,13 +10,19 @@ seed cycling 0, 1, 2 over the steps.  Metric: Gray-code terms per second
 resident in HBM; the L2 (129 MB) is flushed between steps by writing 256 MB.
 
 The JSON line also carries: the end-to-end rate through the C ABI from pinned
-host buffers (copies inside the timed region), the roofline of the dominant
-kernel against the FP64 peak derived from SM count x 4 FP64 flop/clk/SM x max
-SM clock, the SM clocks sampled during the timed region, and the CPU oracle's
-rate on a bounded sample (rank 0, N = 1).
+host buffers (copies inside the timed region); the roofline of the dominant
+kernel against the FP64 peak measured on the same GPU by the DFMA probe
+(``perm_fp64_fma_probe``; the peak derived from SM count x 4 FP64 flop/clk/SM x
+max SM clock beside it); Glynn and Ryser apart (terms/s, error of the timed n = 32
+results against stored quad-oracle values); the SM clocks sampled during the
+timed region; the CPU oracle's FP64 Gray-order Glynn (double-double sum) on full
+permanents at n = 20-32 on all host cores (rank 0, N = 1); and the other forms
+(precision rungs, batch, adjoint, collisions, row minors, draws, and single
+Glynn permanents at n = 20, 36 and 40 against stored oracle values).
 
 ``--impl reference`` times the CPU oracle (the only reference implementation of
-this method here) on the same workload, one bounded sample per item and step.
+this method here: FP64 Gray-order Glynn / Ryser partial sums with double-double
+accumulation) on the same workload, one bounded sample per item and step.
 
 Multi-GPU (torchrun): every rank runs the same sweep on its own GPU — the
 permanents are independent problems, so there is no data-path collective; the
@@ -54,9 +60,13 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / compensated / adjoint forms")
-    ap.add_argument("--form", choices=["sweep", "batched", "adjoint", "sampler"], default="sweep",
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the single n = 36 and n = 40 Glynn launches (about 3.7 minutes together)")
+    ap.add_argument("--form", choices=["sweep", "batched", "adjoint", "sampler", "shard"], default="sweep",
                     help="sweep = the metric above (default); batched / adjoint / sampler time only that "
-                         "form (for profiling) and print its own JSON line")
+                         "form (for profiling) and print its own JSON line; shard = one Glynn permanent "
+                         "of --shard-n split over the ranks' Gray ranges with one exchange of partials")
+    ap.add_argument("--shard-n", type=int, default=36)
     ap.add_argument("--batched-count", type=int, default=4096)
     ap.add_argument("--adjoint-n", type=int, default=24)
     ap.add_argument("--adjoint-batch", type=int, default=64)
@@ -190,32 +200,31 @@ def measured_traffic(n: int):
 # ---------------------------------------------------------------------------
 # the oracle on the host cores
 # ---------------------------------------------------------------------------
-def oracle_rate(items, seconds: float, threads: int):
-    """Oracle terms/s over bounded Gray-index samples of the given items."""
+def oracle_sample_fn(kind):
+    """The oracle's FP64 Gray-order partial sum (double-double accumulation) for a method."""
+    import oracle
+    return oracle.glynn_f64dd_range if kind == "glynn" else oracle.ryser_f64dd_range
+
+
+def oracle_full_rate(ns, seconds: float, threads: int):
+    """Oracle FP64 Glynn terms/s on full permanents of the sweep's seed-0 inputs:
+    every n of ``ns`` once, then again from the smallest while the total stays
+    below ``seconds``."""
     import oracle
     import synthetic as S
 
-    mats = {(n, seed): S.gaussian(n, seed) for _, n, seed in items}
-
-    def run(sample):
+    done, spent, runs = 0, 0.0, []
+    for n in sorted(ns):
+        A = S.gaussian(n, 0)
         t0 = time.perf_counter()
-        done = 0
-        for kind, n, seed in items:
-            cnt = min(sample, terms_of(kind, n))
-            f = oracle.glynn_range if kind == "glynn" else oracle.ryser_range
-            f(mats[(n, seed)], 0, cnt, gray=True, threads=threads)
-            done += cnt
-        return done, time.perf_counter() - t0
-
-    sample = 64
-    done, dt = run(sample)
-    while dt < seconds / 8 and sample < (1 << 40):
-        sample *= 2
-        done, dt = run(sample)
-    if dt < seconds:
-        sample = int(sample * seconds / max(dt, 1e-6))
-        done, dt = run(sample)
-    return done / dt, sample, dt
+        oracle.glynn_f64dd(A, threads=threads)
+        dt = time.perf_counter() - t0
+        done += 2 ** (n - 1)
+        spent += dt
+        runs.append((n, dt))
+        if spent > seconds:
+            break
+    return done / spent, runs, spent
 
 
 def run_reference(args):
@@ -225,37 +234,44 @@ def run_reference(args):
     ns, kinds = workload(args)
     threads = os.cpu_count() or 1
     per_step = max(args.cpu_seconds, 1.0) / 3.0
-    # calibrate one bounded sample per item so that a step costs ~per_step seconds
-    items0 = step_items(ns, kinds, 0)
-    _, sample, _ = oracle_rate(items0, per_step / 4, threads)
-    import oracle
     import synthetic as S
 
-    def one_step(step):
+    mats = {(n, seed): S.gaussian(n, seed) for n in ns for seed in range(3)}
+
+    def one_step(step, sample):
         items = step_items(ns, kinds, step)
         t0 = time.perf_counter()
         done = 0
         for kind, n, seed in items:
             cnt = min(sample, terms_of(kind, n))
-            f = oracle.glynn_range if kind == "glynn" else oracle.ryser_range
-            f(S.gaussian(n, seed), 0, cnt, gray=True, threads=threads)
+            oracle_sample_fn(kind)(mats[(n, seed)], 0, cnt, threads=threads)
             done += cnt
         return done, time.perf_counter() - t0
 
+    # calibrate one bounded sample per item (the first terms in Gray order) so
+    # that a step costs about per_step seconds
+    sample = 1 << 16
+    while True:
+        d, t = one_step(0, sample)
+        if t > per_step / 4 or sample >= (1 << 40):
+            break
+        sample *= 2
+    sample = max(1, int(sample * per_step / max(t, 1e-6)))
+
     for w in range(args.warmup):
-        one_step(w)
+        one_step(w, sample)
     tot_terms, tot_t = 0, 0.0
     for s in range(args.steps):
-        d, t = one_step(s)
+        d, t = one_step(s, sample)
         tot_terms += d
         tot_t += t
     value = tot_terms / tot_t
-    sample_desc = ("oracle quad-precision Gray-order partial sums, first %d terms of each (method, n) item per step"
-                   % sample)
+    sample_desc = ("oracle FP64 Gray-order partial sums (double-double accumulation), first %d terms of each "
+                   "(method, n) item per step, %d threads" % (sample, threads))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / max(args.steps, 1),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f128 (oracle)",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 (oracle, dd sum)",
         "data": "synthetic", "config": config_dict(args, ns, kinds, 1),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample_desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -268,7 +284,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # the other forms, each against the plain form on the same GPU
 # ---------------------------------------------------------------------------
-def measure_forms(dev, plain_rate):
+def measure_forms(dev, plain_rate, peak_fp64, large=True):
     """The other forms of the method on the same GPU: precision rungs, the batched
     form (graph replay), the adjoint, photon collisions, row minors and
     boson-sampling draws, each with its parity figure.  A failing section is
@@ -420,9 +436,40 @@ def measure_forms(dev, plain_rate):
                           "cost_per_draw_in_glynn_n24": ts / ns / t24, "launches_per_replay": 2 * n - 1,
                           "draws_equal_oracle_m30_n8": same}
 
+    def single_sizes():
+        # one FP64 Glynn permanent per launch across the metric's n = 20-40 (the
+        # sweep's seed-0 Gaussian inputs), each against a stored oracle value; the
+        # error is that of the timed launch's own result (a second n = 40 pass
+        # would cost minutes)
+        for n in ([20, 36, 40] if large else [20]):
+            Ah = S.gaussian(n, 0)
+            dA = torch.as_tensor(Ah).to(dev)
+            held = {}
+
+            def run():
+                held["out"] = pg.glynn(dA)
+
+            if n == 20:
+                ref = refs["glynn_gaussian_n20"]
+                run()
+                reps = 50
+                t = timed(lambda: [run() for _ in range(reps)]) / reps
+                src = "quad Glynn (bench_refs.json)"
+            else:
+                r = large_ref("gaussian", n, 0)
+                ref = {"sha": r[0], "value": list(r[1])} if r else None
+                pg.glynn_range(dA, 0, 1 << 16)  # loads the n-sized kernel without a full pass
+                t = timed(run)
+                src = "FP64 + double-double Glynn (large_refs.tsv)"
+            got = complex(held["out"].cpu().item())
+            fl = flops_per_term(n) * 2 ** (n - 1) / t
+            forms["glynn_single_n%d" % n] = {
+                "terms_per_s": 2 ** (n - 1) / t, "s": t, "tflops": fl / 1e12, "frac_of_fp64_peak": fl / peak_fp64,
+                "rel_err_vs_oracle": ref_rel_err(ref, Ah, got) if ref else None, "oracle": src}
+
     for name, fn in (("glynn_n32", ladder), ("batched_4096_n8-24", batched), ("adjoint", adjoint),
                      ("collisions_n28", collisions), ("row_minors_k32", minors),
-                     ("boson_sample_m1000_n24_x16", sampler)):
+                     ("boson_sample_m1000_n24_x16", sampler), ("glynn_single", single_sizes)):
         try:
             fn()
         except Exception as e:  # one form failing must not take the bench line down
@@ -467,6 +514,90 @@ def sampler_case(pg, U, n, ns, seed, dev, prec="fp64"):
     smp = pg.BosonSampler(torch.as_tensor(U).to(dev), list(range(n)), ns, prec=prec)
     smp.load(torch.as_tensor(alpha).to(dev), torch.as_tensor(uu).to(dev))
     return smp, alpha, uu
+
+
+def fp64_peak(dev, gpu_index: int, sms: int):
+    """FP64 peak measured on this GPU: the DFMA probe (perm_fp64_fma_probe, 4 x SMs
+    blocks of 256 threads, 4 independent FMA chains per thread), best of 8
+    launches timed with CUDA events, SM clocks sampled meanwhile.  None if the
+    probe fails (the derived peak is used then)."""
+    import torch
+
+    import paper_1606_05836_gb300 as pg
+
+    grid, block, iters = 4 * sms, 256, 1 << 16
+    try:
+        pg.fp64_fma_probe(256, grid, block, dev)
+        torch.cuda.synchronize(dev)
+        clk = ClockSampler(gpu_index)
+        clk.start()
+        best, fmas = None, 0
+        for _ in range(8):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fmas = pg.fp64_fma_probe(iters, grid, block, dev)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            t = e0.elapsed_time(e1) / 1e3
+            best = t if best is None else min(best, t)
+        c = clk.stop()
+    except Exception:  # the probe is a diagnostic: fall back to the derived peak
+        return None
+    return {"flops_per_s": 2.0 * fmas / best, "dfma_per_s": fmas / best, "s_per_launch": best,
+            "grid": grid, "block": block, "iters": iters, "chains": 4,
+            "sm_mhz": c["sm_mhz"] if c else None, "reasons": c["reasons"] if c else None}
+
+
+def sweep_refs():
+    """{(n, seed): (sha, (re_hi, re_lo, im_hi, im_lo))} of the quad-oracle values of
+    the sweep's inputs (tests/golden/sweep_refs.tsv, written by make_sweep_refs.py)."""
+    out = {}
+    path = os.path.join(ROOT, "tests", "golden", "sweep_refs.tsv")
+    with open(path) as f:
+        for line in f:
+            p = line.rstrip("\n").split("\t")
+            if not p[0].isdigit() or p[7] != "glynn_gray":
+                continue
+            out[(int(p[0]), int(p[1]))] = (p[2], tuple(float(x) for x in p[3:7]))
+    return out
+
+
+def large_ref(kind: str, n: int, seed: int):
+    """(sha, (re_hi, re_lo, im_hi, im_lo)) of tests/golden/large_refs.tsv (FP64 /
+    double-double oracle, make_large_refs.py), or None if not stored."""
+    path = os.path.join(ROOT, "tests", "golden", "large_refs.tsv")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        for line in f:
+            p = line.rstrip("\n").split("\t")
+            if len(p) >= 8 and p[0] == kind and p[1] == str(n) and p[2] == str(seed):
+                return p[3], tuple(float(x) for x in p[4:8])
+    return None
+
+
+def method_rates(per_kind, results, nmax: int):
+    """Glynn and Ryser apart: terms/s over all their timed launches, and the error
+    of their timed n = nmax results against the stored quad-oracle values."""
+    import synthetic as S
+
+    refs = sweep_refs()
+    bars = {"glynn": "1e-10 (FP64 Glynn)",
+            "ryser": "none: FP64 Ryser loses digits to cancellation (the paper's finding; stated ~1e-6 at n = 32)"}
+    out = {}
+    for kind, (terms, ms) in per_kind.items():
+        errs = {}
+        for (k, n, seed), t in results.items():
+            if k != kind or n != nmax or (n, seed) not in refs:
+                continue
+            sha, v = refs[(n, seed)]
+            e = ref_rel_err({"sha": sha, "value": list(v)}, S.gaussian(n, seed), complex(t.cpu().item()))
+            if e is not None:
+                errs["n%d_seed%d" % (n, seed)] = e
+        out[kind] = {"terms_per_s": terms / (ms / 1e3) if ms > 0 else None, "launches_ms": ms,
+                     "rel_err_vs_quad_oracle": errs, "max_rel_err": max(errs.values()) if errs else None,
+                     "bar": bars.get(kind)}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -525,26 +656,33 @@ def run_ours(args):
         sampler.start()
     step_ms = []
     dom = []  # (flops, ms) of the dominant kernel's launches
+    per_kind = {k: [0, 0.0] for k in kinds}  # terms, ms of every launch of the method
+    results = {}  # (kind, n, seed) -> the permanent the timed launch returned
     terms_total = 0
     launches = 0
     for s in range(args.steps):
         flush.zero_()
         items = step_items(ns, kinds, s)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in items]
+        outs = []
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for (kind, n, seed), (a, b) in zip(items, ev):
             a.record(stream)
-            fn[kind](dmat[(n, seed)], prec=args.prec)
+            outs.append(fn[kind](dmat[(n, seed)], prec=args.prec))
             b.record(stream)
             terms_total += terms_of(kind, n)
             launches += 1
         e1.record(stream)
         torch.cuda.synchronize(dev)
         step_ms.append(e0.elapsed_time(e1))
-        for (kind, n, seed), (a, b) in zip(items, ev):
+        for (kind, n, seed), (a, b), out in zip(items, ev, outs):
+            ms = a.elapsed_time(b)
+            per_kind[kind][0] += terms_of(kind, n)
+            per_kind[kind][1] += ms
+            results[(kind, n, seed)] = out
             if n == nmax:
-                dom.append((flops_per_term(n) * terms_of(kind, n), a.elapsed_time(b)))
+                dom.append((flops_per_term(n) * terms_of(kind, n), ms))
     torch.cuda.synchronize(dev)
     clocks = sampler.stop() if sampler else None
     t_dev = max_over_ranks(sum(step_ms) / 1e3)
@@ -593,7 +731,9 @@ def run_ours(args):
     sms = props.multi_processor_count
     sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     # GB300: 2 FP64 FMA lanes per clock per SM (0.5 per sub-partition) = 4 flop/clk/SM
-    peak_fp64 = sms * 4 * sm_max_mhz * 1e6
+    peak_derived = sms * 4 * sm_max_mhz * 1e6
+    probe = fp64_peak(dev, local, sms)
+    peak_fp64 = probe["flops_per_s"] if probe else peak_derived
     achieved = sum(f for f, _ in dom) / (sum(ms for _, ms in dom) / 1e3) if dom else None
     traffic = measured_traffic(nmax)
     roofline = {
@@ -601,27 +741,35 @@ def run_ours(args):
         "kernel": "fwd_kernel<N=%d> (Glynn+Ryser, %s)" % (nmax, args.prec),
         "achieved": achieved / 1e12 if achieved else None, "peak": peak_fp64 / 1e12, "unit": "TFLOP/s",
         "frac": (achieved / peak_fp64) if achieved else None,
-        "peak_source": "derived: %d SMs x 4 FP64 flop/clk/SM x %.0f MHz" % (sms, sm_max_mhz),
+        "peak_source": ("measured: FP64 FMA probe (perm_fp64_fma_probe), %.0f MHz median SM clock during it"
+                        % probe["sm_mhz"] if probe else
+                        "derived: %d SMs x 4 FP64 flop/clk/SM x %.0f MHz" % (sms, sm_max_mhz)),
+        "peak_derived": peak_derived / 1e12,
+        "frac_of_derived": (achieved / peak_derived) if achieved else None,
+        "peak_probe": probe,
         "flops_per_term": "8n-4 (2n update + 6(n-1) product + 2 accumulate)",
         "traffic": traffic,
     }
+    by_method = method_rates(per_kind, results, nmax)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        items = step_items(ns, kinds, 0)
-        rate, sample, dt = oracle_rate(items, args.cpu_seconds, threads)
+        rate, runs, dt = oracle_full_rate([20, 24, 28, 32], args.cpu_seconds, threads)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": "quad-precision oracle, first %d Gray-order terms of each (method, n) item of step 0, "
-                         "%.1f s" % (sample, dt)}
+               "sample": "oracle FP64 Gray-order Glynn with double-double accumulation (glynn_f64dd), full "
+                         "permanents of the sweep's seed-0 Gaussian inputs at n = %s, %.1f s on %d threads"
+                         % (",".join(str(n) for n, _ in runs), dt, threads),
+               "per_n_terms_per_s": {str(n): 2 ** (n - 1) / t for n, t in runs}}
     forms = None
     if world == 1 and not args.no_forms:
-        forms = measure_forms(dev, value)
+        forms = measure_forms(dev, value, peak_fp64, not args.no_large)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec != "fp32p_dd" else "f64+f32",
         "data": "synthetic", "config": config_dict(args, ns, kinds, world), "roofline": roofline,
-        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "forms": forms,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "by_method": by_method,
+        "forms": forms,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -690,10 +838,63 @@ def run_single_form(args):
     return 0
 
 
+def run_shard(args):
+    """One Glynn permanent (the sweep's seed-0 Gaussian input of size --shard-n)
+    split over the ranks as Algorithm 2 splits its iteration range: each rank one
+    contiguous Gray range on its own GPU (perm_glynn_range), then one all-gather of
+    the 32-byte partials and perm_combine_partials on every rank.  Timed from a
+    barrier to the combined result on every rank (max over ranks); prints one JSON
+    line on rank 0 with the rate and the error against the stored oracle value."""
+    import torch
+
+    import paper_1606_05836_gb300 as pg  # noqa: F401  (loads the library)
+    import synthetic as S
+    from paper_1606_05836_gb300 import shard
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    n = args.shard_n
+    Ah = S.gaussian(n, 0)
+    dA = torch.as_tensor(Ah).to(dev)
+    fn = shard.gpu_partial_fn(dA, "glynn")
+    fn(0, 1 << 12)  # loads the kernel
+    times, per = [], None
+    for _ in range(max(1, args.steps)):
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        per = shard.sharded_permanent(n, "glynn", fn, rank, world)
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        times.append(dt)
+    if rank == 0:
+        r = large_ref("gaussian", n, 0)
+        err = ref_rel_err({"sha": r[0], "value": list(r[1])}, Ah, per) if r else None
+        t = min(times)
+        print(json.dumps({"form": "shard", "n": n, "n_gpus": world, "steps": len(times), "s": t,
+                          "terms_per_s": 2 ** (n - 1) / t, "exchange": "all-gather of 32-byte partials" if world > 1
+                          else "none (one rank)", "rel_err_vs_oracle": err, "scaling": "strong"}), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.form == "shard":
+        return run_shard(args)
     if args.form != "sweep":
         return run_single_form(args)
     return run_ours(args)

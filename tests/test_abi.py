@@ -107,3 +107,20 @@ def test_argument_errors_of_minors_and_draws(lib):
     assert lib.boson_sample(*args(8, 3, ins, 0)) == 0       # no draws: nothing to do
     assert lib.boson_sample(*args(8, 3, ins, 2, u=None)) == -1
     assert lib.boson_sample(*args(8, 3, None, 2)) == -1
+
+
+def test_argument_errors_of_combine_and_probe(lib):
+    """perm_combine_partials validates its arguments (host code only), and the
+    FP64 probe rejects bad launch shapes before any launch."""
+    parts = (ctypes.c_double * 4)(1.0, 0.0, 0.0, 0.0)
+    out = (ctypes.c_double * 4)()
+    assert lib.perm_combine_partials(None, 1, 4, 0, out) == -1
+    assert lib.perm_combine_partials(parts, 0, 4, 0, out) == -1
+    assert lib.perm_combine_partials(parts, 1, 4, 2, out) == -1
+    assert lib.perm_combine_partials(parts, 1, 0, 0, out) == -2
+    assert lib.perm_combine_partials(parts, 1, 4, 0, out) == 0 and out[0] == 1.0 / 8
+    sink = ctypes.c_void_p(256)
+    assert lib.perm_fp64_fma_probe(0, 1, 128, sink, None) == -1
+    assert lib.perm_fp64_fma_probe(1, 1, 100, sink, None) == -1
+    assert lib.perm_fp64_fma_probe(1, 0, 128, sink, None) == -1
+    assert lib.perm_fp64_fma_probe(1, 1, 128, None, None) == -1

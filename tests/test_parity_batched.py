@@ -123,3 +123,34 @@ def test_batched_device_guards_give_nan_not_a_fault(pg):
 def test_batched_empty(pg):
     per, prob = pg.batched([])
     assert per.numel() == 0
+
+
+@pytest.mark.slow
+def test_config4_batch_full_size_against_the_oracle(pg):
+    """The benchmark's batch itself: 4096 output patterns of one Haar 1000 x 1000
+    unitary (n uniform in 8..24, 20 % with repeated output modes), in its launch
+    configuration (one CUDA graph replay of the persistent walk, default shape).
+    Every item of n >= 23 (the ones that dominate its time) and every collision
+    item is compared with the oracle (FP64 Gray-order Glynn with double-double
+    accumulation, pinned against the quad oracle), element by element: Per within
+    1e-10 and the Eq. (1) probability |Per|^2 / prod t_j! within 2e-10 (twice Per's
+    relative error bounds |Per|^2's)."""
+    from paper_1606_05836_gb300 import batch as B
+    U = S.haar_unitary(1000, 0)
+    mats, ns, _, cols, collide = S.batch_patterns(U, 4096, 8, 24, 1)
+    scale = [1.0 / float(np.prod([math.factorial(int(x)) for x in np.bincount(c)])) for c in cols]
+    bp = B.BatchedPermanents(mats, method="glynn", scale=scale)
+    bp.capture()
+    per, prob = bp.replay()
+    per, prob = per.cpu().numpy(), prob.cpu().numpy()
+    check = [i for i in range(len(mats)) if ns[i] >= 23 or collide[i]]
+    assert sum(1 for i in check if ns[i] >= 23) > 300 and int(collide.sum()) > 700
+    worst = 0.0
+    for i in check:
+        want = oracle.glynn_f64dd(mats[i])
+        e = want.rel_err(per[i])
+        worst = max(worst, e)
+        assert e < REL_TOL, (i, int(ns[i]), bool(collide[i]), per[i], want.hi)
+        p_want = abs(want.hi + want.lo) ** 2 * scale[i]
+        assert abs(prob[i] - p_want) <= 2 * REL_TOL * p_want, (i, prob[i], p_want)
+    print("\nconfig-4 batch: %d items checked, max relative error of Per %.2e" % (len(check), worst))

@@ -30,14 +30,15 @@ def test_minors_vs_oracle(pg, n):
     per, abs2, M, G = pg.grad(to_dev(A), minor=True, grad_abs2=True)
     want_p = oracle.ryser(A) if n > 0 else None
     assert want_p.rel_err(complex(per.cpu().item())) < REL_TOL
-    assert abs(abs2.item() - abs(want_p.hi) ** 2) <= 1e-9 * abs(want_p.hi) ** 2
+    # |Per|^2 and 2 Per conj(M) combine two computed factors: twice the bar
+    assert abs(abs2.item() - abs(want_p.hi) ** 2) <= 2 * REL_TOL * abs(want_p.hi) ** 2
     if n == 1:
         assert complex(M.cpu()[0, 0].item()) == 1.0
         return
     W = oracle.minors(A)
     assert normwise(M.cpu().numpy(), W) < REL_TOL
     Gw = 2 * want_p.hi * np.conj(W)
-    assert normwise(G.cpu().numpy(), Gw) < 1e-9
+    assert normwise(G.cpu().numpy(), Gw) < 2 * REL_TOL
 
 
 def test_minors_sampled_n20(pg):
@@ -47,7 +48,7 @@ def test_minors_sampled_n20(pg):
     for i, j in [(0, 0), (3, 17), (19, 19), (11, 4)]:
         sub = np.delete(np.delete(A, i, axis=0), j, axis=1)
         want = oracle.ryser(sub)
-        assert want.rel_err(M[i, j]) < 1e-9
+        assert want.rel_err(M[i, j]) < REL_TOL
 
 
 @pytest.mark.parametrize("n", [6, 12])
@@ -105,8 +106,8 @@ def test_autograd_function(pg):
     y.backward()
     P = oracle.ryser(A).hi
     W = oracle.minors(A)
-    assert abs(y.item() - abs(P) ** 2) <= 1e-9 * abs(P) ** 2
-    assert normwise(t.grad.cpu().numpy(), 2 * P * np.conj(W)) < 1e-9
+    assert abs(y.item() - abs(P) ** 2) <= 2 * REL_TOL * abs(P) ** 2
+    assert normwise(t.grad.cpu().numpy(), 2 * P * np.conj(W)) < 2 * REL_TOL
     # batched, with a non-trivial upstream gradient
     mats = to_dev(np.stack([S.gaussian(7, 970 + b, 1.0) for b in range(3)])).requires_grad_(True)
     w = torch.tensor([0.5, -2.0, 3.0], dtype=torch.float64, device="cuda")
@@ -114,4 +115,4 @@ def test_autograd_function(pg):
     for b in range(3):
         Ab = mats[b].detach().cpu().numpy()
         want = w[b].item() * 2 * oracle.ryser(Ab).hi * np.conj(oracle.minors(Ab))
-        assert normwise(mats.grad[b].cpu().numpy(), want) < 1e-9
+        assert normwise(mats.grad[b].cpu().numpy(), want) < 2 * REL_TOL

@@ -5,14 +5,17 @@ cudaMalloc because it can synchronise the device).  Its scratch is a fixed array
 inside libperm.
 
 Called through the C ABI (ctypes) and compared with perm_glynn, the entry point
-that takes a caller workspace, on two calls in a row.  This file is collected
-last on purpose; it also passes on its own in a fresh process.
+that takes a caller workspace, on two calls in a row, and with the CPU oracle
+(quad precision) on calls that alternate between two matrices, so that partial
+sums left in the shared array by one call cannot pass for the next one's.  This
+file is collected last on purpose; it also passes on its own in a fresh process.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import synthetic as S
 
 pytestmark = pytest.mark.gpu
@@ -70,6 +73,21 @@ def test_noalloc_matches_workspace_entry_point_twice(lib, n, seed):
         assert st == 0, st
         got = complex(out.cpu().item())
         assert abs(got - want) <= REL_TOL * abs(want), (got, want)
+
+
+def test_noalloc_against_the_oracle_alternating_matrices(lib):
+    """Two different n = 20 matrices, A B A B: every result within 1e-10 of the
+    quad-precision Glynn oracle."""
+    import torch
+    stream = torch.cuda.current_stream().cuda_stream
+    mats = [S.gaussian(20, 31), S.gaussian(20, 32)]
+    want = [oracle.glynn(A) for A in mats]
+    devs = [_dev(A) for A in mats]
+    for call in range(4):
+        k = call % 2
+        st, out = _glynn_noalloc(lib, devs[k], 20, stream)
+        assert st == 0, st
+        assert want[k].rel_err(complex(out.cpu().item())) < REL_TOL, (call, k)
 
 
 def test_noalloc_rejects_grid_beyond_its_scratch(lib):
