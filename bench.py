@@ -62,11 +62,16 @@ def parse_args():
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / compensated / adjoint forms")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the single n = 36 and n = 40 Glynn launches (about 3.7 minutes together)")
-    ap.add_argument("--form", choices=["sweep", "batched", "adjoint", "sampler", "shard"], default="sweep",
+    ap.add_argument("--form", choices=["sweep", "batched", "adjoint", "sampler", "shard", "range"], default="sweep",
                     help="sweep = the metric above (default); batched / adjoint / sampler time only that "
                          "form (for profiling) and print its own JSON line; shard = one Glynn permanent "
-                         "of --shard-n split over the ranks' Gray ranges with one exchange of partials")
+                         "of --shard-n split over the ranks' Gray ranges with one exchange of partials; range = "
+                         "one Glynn partial sum over the first 2^--range-log2 Gray indices at n = --range-n "
+                         "(a shard-sized unit of a large permanent, for profiling)")
     ap.add_argument("--shard-n", type=int, default=36)
+    ap.add_argument("--range-n", type=int, default=40,
+                    help="--form range: size of the matrix whose first 2^--range-log2 Gray terms are summed")
+    ap.add_argument("--range-log2", type=int, default=30)
     ap.add_argument("--batched-count", type=int, default=4096)
     ap.add_argument("--adjoint-n", type=int, default=24)
     ap.add_argument("--adjoint-batch", type=int, default=64)
@@ -784,7 +789,22 @@ def run_single_form(args):
     import synthetic as S
 
     dev = torch.device("cuda", 0)
-    if args.form == "sampler":
+    if args.form == "range":
+        n, L = args.range_n, args.range_log2
+        dA = torch.as_tensor(S.gaussian(n, 0)).to(dev)
+        for _ in range(args.warmup):
+            pg.glynn_range(dA, 0, 1 << 12)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            pg.glynn_range(dA, 0, 1 << L)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        t = e0.elapsed_time(e1) / 1e3 / max(args.steps, 1)
+        print(json.dumps({"form": "range", "n": n, "terms": 1 << L, "steps": args.steps, "s": t,
+                          "terms_per_s": (1 << L) / t, "tflops": (8 * n - 4) * (1 << L) / t / 1e12}), flush=True)
+    elif args.form == "sampler":
         m, n, ns = args.sampler_m, args.sampler_n, args.sampler_count
         smp, _, _ = sampler_case(pg, S.haar_unitary(m, 0), n, ns, 5, dev)
         for _ in range(args.warmup):

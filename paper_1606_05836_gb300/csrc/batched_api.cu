@@ -26,6 +26,97 @@ __device__ inline long long block_scan_incl(long long v, long long* sh) {
   return r;
 }
 
+// Per item (one warp each): bitwise-identical columns are one group; with any
+// group of two or more copies (and use_mult) the item gets the column structure
+// of the multiplicity expansion of Eq. (S2) — the delta = +1 copy from the first
+// singleton group, else from the first smallest group; singletons are free
+// columns, a group of m copies enters through its number k of -1 signs (radix
+// m + 1, or m for the group holding the fixed copy) — and its index space is
+// classes x 2^free.  Otherwise g = 0 and the index space is 2^M.
+__global__ void __launch_bounds__(32) batch_mult_kernel(BatchArgs a) {
+  const int lane = threadIdx.x;
+  for (int item = blockIdx.x; item < a.count; item += gridDim.x) {
+    const int n = a.ns[item];
+    MultInfo* mi = a.mult + item;
+    if (n < 1 || n > BATCH_MAX_N) {  // the planner reports it; keep the workspace sane
+      if (lane == 0) {
+        mi->g = 0;
+        a.terms[item] = 1;
+      }
+      continue;
+    }
+    const double2* A = a.packed + a.offsets[item];
+    int rep = lane;  // smallest column index with the same entries
+    if (a.use_mult && lane < n) {
+      for (int c = 0; c < lane; c++) {
+        bool same = true;
+        for (int i = 0; i < n && same; i++) {
+          const double2 x = A[i * n + lane], y = A[i * n + c];
+          same = (__double_as_longlong(x.x) == __double_as_longlong(y.x)) &&
+                 (__double_as_longlong(x.y) == __double_as_longlong(y.y));
+        }
+        if (same) {
+          rep = c;
+          break;
+        }
+      }
+    }
+    __shared__ int reps[BATCH_MAX_N];
+    reps[lane] = rep;
+    __syncwarp();
+    if (lane == 0) {
+      int mult[BATCH_MAX_N], col[BATCH_MAX_N], g = 0;
+      bool repeated = false;
+      for (int j = 0; j < n; j++) {
+        if (reps[j] == j) {
+          col[g] = j;
+          mult[g++] = 1;
+        } else {
+          for (int c = 0; c < g; c++)
+            if (col[c] == reps[j]) {
+              mult[c]++;
+              repeated = true;
+            }
+        }
+      }
+      const int M = batch_M(n, a.kind);
+      if (!a.use_mult || !repeated) {
+        mi->g = 0;
+        a.terms[item] = 1ll << M;
+      } else {
+        int fixed = -1;
+        for (int c = 0; c < g && fixed < 0; c++)
+          if (mult[c] == 1) fixed = c;
+        if (fixed < 0) {
+          fixed = 0;
+          for (int c = 1; c < g; c++)
+            if (mult[c] < mult[fixed]) fixed = c;
+        }
+        int nfree = 0;
+        long long classes = 1;
+        for (int c = 0; c < g; c++) {
+          mi->mult[c] = (unsigned char)mult[c];
+          mi->radix[c] = 0;
+          mi->radix_base[c] = 1;
+          if (mult[c] == 1) {
+            mi->role[c] = (signed char)((c == fixed) ? -1 : nfree++);
+          } else {
+            mi->role[c] = -2;
+            mi->radix[c] = (unsigned char)((c == fixed) ? mult[c] : mult[c] + 1);
+            mi->radix_base[c] = classes;
+            classes *= mi->radix[c];
+          }
+          a.mcol[item * BATCH_MAX_N + c] = (signed char)col[c];
+        }
+        mi->nfree = nfree;
+        mi->g = g;
+        a.terms[item] = classes << nfree;
+      }
+    }
+    __syncwarp();
+  }
+}
+
 __global__ void __launch_bounds__(BATCH_PLAN_THREADS) batch_plan_kernel(BatchArgs a) {
   __shared__ int hist[BATCH_MAX_N + 1];
   __shared__ int base[BATCH_MAX_N + 1];
@@ -67,12 +158,12 @@ __global__ void __launch_bounds__(BATCH_PLAN_THREADS) batch_plan_kernel(BatchArg
   const int seg = (a.count + P - 1) / P;
   const int lo = t * seg, hi = min(a.count, lo + seg);
   long long mine = 0;
-  for (int p = lo; p < hi; p++) mine += batch_units(batch_M(a.ns[a.order[p]], a.kind), a.unit_log2);
+  for (int p = lo; p < hi; p++) mine += batch_units(a.terms[a.order[p]], a.unit_log2);
   long long incl = block_scan_incl(mine, sh);
   long long run = incl - mine;
   for (int p = lo; p < hi; p++) {
     a.unit_start[p] = run;
-    run += batch_units(batch_M(a.ns[a.order[p]], a.kind), a.unit_log2);
+    run += batch_units(a.terms[a.order[p]], a.unit_log2);
   }
   const long long total_units = sh[P - 1 < 0 ? 0 : P - 1];
   __syncthreads();
@@ -118,19 +209,33 @@ __global__ void __launch_bounds__(128) batch_prep_kernel(BatchArgs a) {
       s_row[i] = s;
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-      const int i = idx % n, j = idx / n;
-      const double f = pow2_double(s_row[i]);
-      const double2 v = A[i * n + j];
-      C[j * n + i] = make_double2(v.x * f, v.y * f);
-      if (a.kind == KIND_GLYNN && j >= 1) {
-        const double sr = 2.0 * v.x * f, si = 2.0 * v.y * f;
-        if (a.prec == PERM_FP32X2) {
-          // R4 walks add the step columns in double-float (16 bytes, same slot)
-          const df re = f64_to_df(sr), im = f64_to_df(si);
-          reinterpret_cast<float4*>(C)[n * n + (j - 1) * n + i] = make_float4(re.h, re.l, im.h, im.l);
-        } else {
-          C[n * n + (j - 1) * n + i] = make_double2(sr, si);
+    const MultInfo* mi = a.mult + item;
+    if (a.use_mult && mi->g > 0) {
+      // repeated columns: the g distinct columns, then the doubled free ones by free index
+      const int g = mi->g;
+      for (int idx = threadIdx.x; idx < n * g; idx += blockDim.x) {
+        const int i = idx % n, c = idx / n;
+        const double f = pow2_double(s_row[i]);
+        const double2 v = A[i * n + a.mcol[item * BATCH_MAX_N + c]];
+        C[c * n + i] = make_double2(v.x * f, v.y * f);
+        const int role = mi->role[c];
+        if (role >= 0) C[n * n + role * n + i] = make_double2(2.0 * v.x * f, 2.0 * v.y * f);
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int i = idx % n, j = idx / n;
+        const double f = pow2_double(s_row[i]);
+        const double2 v = A[i * n + j];
+        C[j * n + i] = make_double2(v.x * f, v.y * f);
+        if (a.kind == KIND_GLYNN && j >= 1) {
+          const double sr = 2.0 * v.x * f, si = 2.0 * v.y * f;
+          if (a.prec == PERM_FP32X2) {
+            // R4 walks add the step columns in double-float (16 bytes, same slot)
+            const df re = f64_to_df(sr), im = f64_to_df(si);
+            reinterpret_cast<float4*>(C)[n * n + (j - 1) * n + i] = make_float4(re.h, re.l, im.h, im.l);
+          } else {
+            C[n * n + (j - 1) * n + i] = make_double2(sr, si);
+          }
         }
       }
     }
@@ -192,7 +297,8 @@ int bfail(cudaError_t e) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t cursor, status, total_units, order, pos, unit_start, prep_off, scale_exp, partials, prep, total;
+  size_t cursor, status, total_units, order, pos, unit_start, prep_off, scale_exp, terms, mult, mcol, partials, prep,
+      total;
   long long units_cap, prep_cap;
 };
 
@@ -213,7 +319,7 @@ int make_layout(int count, const int32_t* hN, int kind, int unit_log2, Layout* L
   for (int i = 0; i < count; i++) {
     const int n = hN[i];
     if (n < 1 || n > BATCH_MAX_N) return PERM_ERANGE;
-    units += batch_units(batch_M(n, kind), unit_log2);
+    units += batch_units(1ll << batch_M(n, kind), unit_log2);
     prep += batch_prep_elems(n, kind);
   }
   size_t off = 0;
@@ -226,6 +332,9 @@ int make_layout(int count, const int32_t* hN, int kind, int unit_log2, Layout* L
   L->unit_start = off; off = align256(off + 8 * ((size_t)count + 1));
   L->prep_off = off; off = align256(off + 8 * (size_t)count);
   L->scale_exp = off; off = align256(off + 4 * (size_t)count);
+  L->terms = off; off = align256(off + 8 * (size_t)count);
+  L->mult = off; off = align256(off + sizeof(MultInfo) * (size_t)count);
+  L->mcol = off; off = align256(off + BATCH_MAX_N * (size_t)count);
   L->partials = off; off = align256(off + 32 * (size_t)units);
   L->prep = off; off = align256(off + 16 * (size_t)prep);
   L->total = off;
@@ -302,6 +411,10 @@ int perm_batched(const perm_c128* dPacked, const int64_t* dOffsets, const int32_
   a.prep_off = (long long*)(w + L.prep_off);
   a.scale_exp = (int*)(w + L.scale_exp);
   a.partials = (double*)(w + L.partials);
+  a.terms = (long long*)(w + L.terms);
+  a.mult = (MultInfo*)(w + L.mult);
+  a.mcol = (signed char*)(w + L.mcol);
+  a.use_mult = (kind == KIND_GLYNN && prec != PERM_FP32X2) ? 1 : 0;
   a.prep = (double2*)(w + L.prep);
   a.units_cap = L.units_cap;
   a.prep_cap = L.prep_cap;
@@ -319,8 +432,11 @@ int perm_batched(const perm_c128* dPacked, const int64_t* dOffsets, const int32_
     if (bps < 1) return bfail(cudaErrorInvalidConfiguration);
     grid = sms * bps;
   }
-  batch_plan_kernel<<<1, BATCH_PLAN_THREADS, 0, s>>>(a);
+  batch_mult_kernel<<<count < 4096 ? count : 4096, 32, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return bfail(e);
+  batch_plan_kernel<<<1, BATCH_PLAN_THREADS, 0, s>>>(a);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return bfail(e);
   const int prep_grid = count < 4096 ? count : 4096;
   batch_prep_kernel<<<prep_grid, 128, 0, s>>>(a);

@@ -122,9 +122,19 @@ int plan_fwd(int n, int kind, uint64_t range, const perm_opts* o, Plan* p) {
   if (grid_opt > 0) {
     p->grid = grid_opt;
   } else {
-    int g = 0;
-    st = full_grid(n, kind, p->prec, p->tune, p->block, &g);
+    // At most two resident blocks per SM (two warps per SM sub-partition keep the
+    // FP64 pipe busy; a third only adds chunk-start recomputation and staging:
+    // measured 2-7 % slower at n = 22-26), and one per SM while a thread would
+    // get fewer than 64 Gray indices (n = 20 Glynn: 156 us instead of 211 us).
+    int sms = 0, bps = 0;
+    st = sm_count(&sms);
     if (st) return st;
+    int e = dispatch_occupancy(n, p->prec, p->tune, p->block, kind, &bps);
+    if (e) return fail_cuda_int(e);
+    if (bps < 1) return fail_cuda(cudaErrorInvalidConfiguration);
+    if (bps > 2) bps = 2;
+    if (range < (uint64_t)sms * (uint64_t)p->block * 64ull) bps = 1;
+    const int g = sms * bps;
     const uint64_t need = (range + (uint64_t)p->block - 1) / (uint64_t)p->block;
     p->grid = (uint64_t)g < need ? g : (int)(need > 0 ? need : 1);
   }

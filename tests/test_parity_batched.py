@@ -154,3 +154,49 @@ def test_config4_batch_full_size_against_the_oracle(pg):
         p_want = abs(want.hi + want.lo) ** 2 * scale[i]
         assert abs(prob[i] - p_want) <= 2 * REL_TOL * p_want, (i, prob[i], p_want)
     print("\nconfig-4 batch: %d items checked, max relative error of Per %.2e" % (len(check), worst))
+
+
+def _repeated(n, mult, seed):
+    """n x n matrix whose columns are g Gaussian columns repeated mult[c] times,
+    in a shuffled column order."""
+    B = S.circular_gaussian((n, len(mult)), seed, 1.0)
+    E = np.repeat(B, mult, axis=1)
+    perm = np.random.default_rng(seed + 1).permutation(n)
+    return np.ascontiguousarray(E[:, perm])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp64_dd", "fp64_df", "fp32x2"])
+def test_batched_repeated_columns_every_structure(pg, prec):
+    """Items with repeated columns (a pair, a triple, several pairs, no singleton
+    at all, every column equal) walk the multiplicity expansion inside the
+    batch (R0-R3; R4 walks the expanded matrix); mixed with plain items, each
+    against the oracle on the expanded matrix."""
+    cases = [(6, [2, 1, 1, 1, 1]), (9, [3, 1, 1, 1, 1, 1, 1]), (12, [2, 2, 2] + [1] * 6), (8, [2, 2, 2, 2]),
+             (7, [7]), (10, [4, 3, 1, 1, 1]), (13, [2] + [1] * 11), (5, [1, 1, 1, 1, 1]), (14, [3, 3, 2] + [1] * 6),
+             (2, [2]), (1, [1]), (11, [5, 6])]
+    mats = [_repeated(n, m, 40 + i) for i, (n, m) in enumerate(cases)]
+    mats += _mixed(6, 3, 12, 9)
+    want = [oracle.perm_def(A) if A.shape[0] <= 8 else oracle.ryser(A) for A in mats]
+    per, _ = pg.batched(mats, method="glynn", prec=prec)
+    got = per.cpu().numpy()
+    tol = REL_TOL
+    for i, w in enumerate(want):
+        assert w.rel_err(got[i]) < tol, (prec, i, mats[i].shape[0], got[i], w.hi)
+    # Ryser does not use the expansion: same values from its plain walk
+    if prec == "fp64":
+        per_r, _ = pg.batched(mats, method="ryser")
+        got_r = per_r.cpu().numpy()
+        for i, w in enumerate(want):
+            assert w.rel_err(got_r[i]) < 1e-9, (i, got_r[i], w.hi)
+
+
+def test_batched_repeated_columns_many_units(pg):
+    """Items of n = 18-22 with repeated columns cut into many small work units
+    (units cross class boundaries and classes span several units)."""
+    cases = [(18, [2] + [1] * 16), (20, [3, 2, 2] + [1] * 13), (22, [2, 2] + [1] * 18), (19, [4, 4, 4, 4, 3])]
+    mats = [_repeated(n, m, 70 + i) for i, (n, m) in enumerate(cases)]
+    for unit_log2 in (2, 5, 11):
+        per, _ = pg.batched(mats, method="glynn", unit_log2=unit_log2)
+        got = per.cpu().numpy()
+        for i, A in enumerate(mats):
+            assert oracle.glynn_f64dd(A).rel_err(got[i]) < REL_TOL, (unit_log2, i)
