@@ -24,8 +24,10 @@ def normwise(M, W):
     return float(np.max(np.abs(M - W)) / np.max(np.abs(W)))
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 12, 14])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 12, 14, 16, 17])
 def test_minors_vs_oracle(pg, n):
+    """All n^2 minors against the oracle's minor permanents; from n = 16 on the
+    kernel prefetches the H column that the next Gray step flips."""
     A = S.gaussian(n, 900 + n, 1.0)
     per, abs2, M, G = pg.grad(to_dev(A), minor=True, grad_abs2=True)
     want_p = oracle.ryser(A) if n > 0 else None
