@@ -358,7 +358,11 @@ def measure_forms(dev, plain_rate, peak_fp64, large=True):
             per8 = per8.cpu().numpy()
             return max(ref_rel_err(r, pick[i], complex(per8[i])) for i, r in enumerate(items))
 
+        walked = [walked_terms(A) for A in mats]
+        wflops = sum(flops_per_term(int(A.shape[0])) * w for A, w in zip(mats, walked))
         forms["batched_4096_n8-24"] = {"terms_per_s": terms / t, "perms_per_s": len(mats) / t, "s_per_replay": t,
+                                       "walked_terms_per_s": sum(walked) / t, "tflops_walked": wflops / t / 1e12,
+                                       "frac_of_fp64_peak": wflops / t / peak_fp64,
                                        "vs_plain_glynn": terms / t / ctx["base"],
                                        "collision_items": int(collide.sum()),
                                        "tuned": {"unit_log2": tuned["unit_log2"], "block": tuned["block"]},
@@ -386,12 +390,18 @@ def measure_forms(dev, plain_rate, peak_fp64, large=True):
         lap = float(np.max(np.abs(np.sum(A0 * M[0].cpu().numpy(), axis=1) - P0)) / abs(P0))
         forms["adjoint_64_n24"] = {"terms_per_s": 64 * 2 ** 23 / tg, "s": tg, "cost_vs_plain_same_batch": tg / tf,
                                    "laplace_identity_rel_err": lap}
-        # n = 32 on a batch of 2 (items run one after another: per-item rate as for 64)
-        G32 = torch.as_tensor(np.stack([S.gaussian(32, b) for b in range(2)])).to(dev)
+        # n = 32, the configured batch of 64 (about 2.3 minutes; --no-large times 2)
+        nb = 64 if large else 2
+        G32 = torch.as_tensor(np.stack([S.gaussian(32, b) for b in range(nb)])).to(dev)
         tg32 = timed(lambda: pg.grad(G32))
-        tf32 = timed(lambda: [pg.glynn(G32[b]) for b in range(2)])
-        forms["adjoint_2_n32"] = {"terms_per_s": 2 * 2 ** 31 / tg32, "s": tg32,
-                                  "cost_vs_plain_same_batch": tg32 / tf32}
+        tf32 = timed(lambda: [pg.glynn(G32[b]) for b in range(min(nb, 8))]) * nb / min(nb, 8)
+        _, _, M32, _ = pg.grad(G32[:1])
+        A32 = G32[0].cpu().numpy()
+        P32 = complex(pg.glynn(G32[0]).cpu().item())
+        lap32 = float(np.max(np.abs(np.sum(A32 * M32[0].cpu().numpy(), axis=1) - P32)) / abs(P32))
+        forms["adjoint_%d_n32" % nb] = {"terms_per_s": nb * 2 ** 31 / tg32, "s": tg32,
+                                        "cost_vs_plain_same_batch": tg32 / tf32,
+                                        "laplace_identity_rel_err": lap32}
 
     def collisions():
         # n = 28: the multiplicity expansion against the plain kernel on the expanded matrix
@@ -480,6 +490,33 @@ def measure_forms(dev, plain_rate, peak_fp64, large=True):
         except Exception as e:  # one form failing must not take the bench line down
             forms[name + "_error"] = "%s: %s" % (type(e).__name__, e)
     return forms
+
+
+def walked_terms(A) -> int:
+    """Gray indices the batched Glynn walk visits for matrix A: 2^(n-1), or with
+    repeated columns the multiplicity expansion's classes x 2^free (the delta = +1
+    copy taken from a singleton column if there is one, else from the smallest
+    group)."""
+    import numpy as np
+
+    n = A.shape[0]
+    _, counts = np.unique(np.ascontiguousarray(A.T).view(np.complex128).reshape(n, n), axis=0,
+                          return_counts=True)
+    counts = sorted(int(c) for c in counts)
+    if max(counts) == 1:
+        return 2 ** (n - 1)
+    singles = counts.count(1)
+    groups = [c for c in counts if c > 1]
+    classes = 1
+    if singles:
+        for m in groups:
+            classes *= m + 1
+        return classes * 2 ** (singles - 1)
+    smallest = groups[0]
+    classes = smallest
+    for m in groups[1:]:
+        classes *= m + 1
+    return classes
 
 
 def bench_refs():

@@ -503,6 +503,24 @@ def test_f64dd_against_quad_at_n32_stored():
         assert abs(qv - fv) <= 1e-12 * abs(qv), seed
 
 
+def test_f64dd_block_diagonal_n36_stored():
+    """n = 36: the stored FP64 / double-double value of a permuted block-diagonal
+    matrix equals the product of its two n = 18 block permanents from the quad
+    oracle (Per(diag(B1, B2)) = Per(B1) Per(B2), invariant under row and column
+    permutations)."""
+    import importlib.util
+    import os
+    from conftest import GOLDEN
+    spec = importlib.util.spec_from_file_location("make_large_refs", os.path.join(GOLDEN, "make_large_refs.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    sha, got = _large_ref("block_diag", 36, 36036)
+    assert mod.digest(mod.make_input("block_diag", 36, 36036)) == sha
+    B1, B2 = mod.block_diag_blocks(36, 36036)
+    want = oracle.glynn_gray(B1).hi * oracle.glynn_gray(B2).hi
+    assert abs(got - want) <= 1e-12 * abs(want)
+
+
 @pytest.mark.slow
 def test_f64dd_n32_recomputed_against_stored_quad():
     """One full n = 32 evaluation (2^31 FP64 terms, ~40 s on 8 cores) of the
