@@ -237,7 +237,9 @@ int perm_grad(const perm_c128* dA, int n, int lda, int batch, int64_t strideA, p
  *   opts->grid above it) is rejected with PERM_ENOMEM.
  * - The first call on each device looks the array's device address up
  *   (cudaGetSymbolAddress) with that device current; make that first call before
- *   any stream capture begins.
+ *   any stream capture begins.  The address is then kept for the life of the
+ *   process: after cudaDeviceReset on that device it is stale, so do not call
+ *   perm_glynn_noalloc in a process that has reset the device.
  * - All calls share the one array, which keeps the previous call's contents
  *   (the ticket is cleared on the stream before each launch).  Calls whose
  *   kernels overlap on the GPU — different streams or host threads without
