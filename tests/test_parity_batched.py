@@ -200,3 +200,14 @@ def test_batched_repeated_columns_many_units(pg):
         got = per.cpu().numpy()
         for i, A in enumerate(mats):
             assert oracle.glynn_f64dd(A).rel_err(got[i]) < REL_TOL, (unit_log2, i)
+
+
+def test_batched_largest_items_against_the_oracle(pg):
+    """Items up to the batched maximum's neighbourhood (n = 25-29, plus a repeated-
+    column item at n = 30) in one launch, each against the FP64 / double-double
+    oracle."""
+    mats = [S.gaussian(n, 500 + n) for n in (25, 27, 29)] + [_repeated(30, [2, 2] + [1] * 26, 530)]
+    per, _ = pg.batched(mats, method="glynn")
+    got = per.cpu().numpy()
+    for i, A in enumerate(mats):
+        assert oracle.glynn_f64dd(A).rel_err(got[i]) < REL_TOL, (i, A.shape[0])

@@ -141,6 +141,19 @@ def test_paper_diag_1pi_n45_range(pg):
         assert hi + lo == (ke - kb) * want
 
 
+def test_max_size_n48_range(pg):
+    """PERM_MAX_N = 48: Gray ranges at the top of the 2^47 index space of a
+    unit-modulus diagonal matrix, where every Glynn term is exactly (1+i)^48 =
+    2^24 (prod delta times the row sums' product), so a range sum is exact."""
+    n = 48
+    A = S.diagonal([1 + 1j] * n)
+    dA = to_dev(A)
+    w = (1 + 1j) ** 48
+    for kb, ke in [(0, 1 << 16), ((1 << 47) - 99991, 1 << 47)]:
+        hi, lo = pair(pg.glynn_range(dA, kb, ke))
+        assert hi + lo == (ke - kb) * w
+
+
 # ---------------------------------------------------------- large-n properties
 def test_block_diagonal_n32(pg):
     B1, B2 = S.gaussian(16, 501), S.gaussian(16, 502)
