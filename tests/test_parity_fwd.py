@@ -311,7 +311,7 @@ def test_sweep_n36_ryser_full_size(pg):
 
 @pytest.mark.slow
 def test_sweep_n40_full_size_vs_stored_oracle(pg):
-    """n = 40, the spec size: the benchmark's seed-0 Gaussian input (2^39
+    """n = 40, the largest size of the sweep: the benchmark's seed-0 Gaussian input (2^39
     Gray terms, ~3.5 min on one GB300) against the stored oracle value within 1e-10."""
     A, want = _large_ref("gaussian", 40, 0)
     got = val(pg.glynn(to_dev(A)))
