@@ -211,8 +211,8 @@ int prob_sample(const perm_c128* dU, int m, int ldu, const int32_t* hS, const in
  * dMinor:    nullable [batch][n][n] dPer/da_ij = Per(A_b without row i, column j).
  * dGradAbs2: nullable [batch][n][n] 2 Per conj(dPer/da_ij) = d|Per|^2/dRe a_ij
  *            + i d|Per|^2/dIm a_ij (PyTorch's convention for a real loss).
- * dWork:     256-byte-aligned, perm_grad_workspace_size() bytes: per lane one n x n
- *            complex accumulator (grid x 128 x n^2 x 16 bytes, e.g. 0.32 GB at
+ * dWork:     256-byte-aligned, perm_grad_workspace_size() bytes: per lane pair one n x n
+ *            complex accumulator (grid x 128 pairs x n^2 x 16 bytes, e.g. 0.32 GB at
  *            n = 32).  The batch runs item after item on `stream`.
  * 1 <= n <= PERM_GRAD_MAX_N (n = 0 gives Per = 1, no derivatives). */
 #define PERM_GRAD_MAX_N 32

@@ -8,7 +8,7 @@
 
 namespace permk {
 
-// One block per (i, j): sum of G_ij over the lanes in a fixed order.
+// One block per (i, j): sum of G_ij over the lane pairs in a fixed order.
 __global__ void __launch_bounds__(256) grad_reduce_kernel(GradReduceArgs r) {
   const int n = r.n;
   const int ij = blockIdx.x;
@@ -41,9 +41,10 @@ __global__ void __launch_bounds__(256) grad_reduce_kernel(GradReduceArgs r) {
       pr = dd_add(pr, dd{r.partials[4 * blk], r.partials[4 * blk + 1]});
       pi = dd_add(pi, dd{r.partials[4 * blk + 2], r.partials[4 * blk + 3]});
     }
+    // both lanes of every pair added each term: one more factor 1/2
     const int sum_s = r.scale_exp[0];
-    const double Pre = ldexp(pr.hi + pr.lo, -sum_s - (n - 1));
-    const double Pim = ldexp(pi.hi + pi.lo, -sum_s - (n - 1));
+    const double Pre = ldexp(pr.hi + pr.lo, -sum_s - (n - 1) - 1);
+    const double Pim = ldexp(pi.hi + pi.lo, -sum_s - (n - 1) - 1);
     // rows were scaled by 2^{s_i}: dPer/da_ij = 2^{s_i - sum s - (n-1)} G'_ij
     const int e = r.scale_exp[1 + i] - sum_s - (n - 1);
     const double mr = ldexp(tr.hi + tr.lo, e);
@@ -127,7 +128,7 @@ int grad_layout(int n, const perm_opts* o, GradLayout* L) {
     grid = sms * bps;
   }
   L->grid = grid;
-  L->P = (long long)grid * GRAD_BLOCK;
+  L->P = (long long)grid * (GRAD_BLOCK / 2);  // lane pairs
   size_t off = 0;
   L->scale_exp = off;
   off = align256(off + sizeof(int) * (size_t)(1 + n));
