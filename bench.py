@@ -237,6 +237,22 @@ def oracle_full_rate(ns, seconds: float, threads: int):
     return done / spent, runs, spent
 
 
+def quad_ryser_times(ns, threads: int):
+    """Seconds of the quad-precision Ryser oracle (Eq. (S1), subsets in binary
+    order with the row sums of every subset formed afresh, as the paper's
+    Algorithm 1 does) on the sweep's seed-0 Gaussian inputs."""
+    import oracle
+    import synthetic as S
+
+    out = {}
+    for n in ns:
+        A = S.gaussian(n, 0)
+        t0 = time.perf_counter()
+        oracle.ryser(A, threads=threads)
+        out[str(n)] = time.perf_counter() - t0
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -398,7 +414,15 @@ def measure_forms(dev, plain_rate, peak_fp64, large=True):
         lap = float(np.max(np.abs(np.sum(A0 * M[0].cpu().numpy(), axis=1) - P0)) / abs(P0))
         forms["adjoint_64_n24"] = {"terms_per_s": 64 * 2 ** 23 / tg, "s": tg, "cost_vs_plain_same_batch": tg / tf,
                                    "laplace_identity_rel_err": lap}
-        # n = 32, the configured batch of 64 (about 2.3 minutes; --no-large times 2)
+        # the same batch through the autograd Function: |Per|^2 forward, gradient backward
+        Gr = G.clone().requires_grad_(True)
+
+        def through_autograd():
+            pg.PermAbs2.apply(Gr).sum().backward()
+
+        ta = timed(through_autograd)
+        forms["adjoint_64_n24"]["autograd_s"] = ta
+        # n = 32, the configured batch of 64 (about 2 minutes; --no-large times 2)
         nb = 64 if large else 2
         G32 = torch.as_tensor(np.stack([S.gaussian(32, b) for b in range(nb)])).to(dev)
         tg32 = timed(lambda: pg.grad(G32))
@@ -838,6 +862,11 @@ def run_ours(args):
                          "permanents of the sweep's seed-0 Gaussian inputs at n = %s, %.1f s on %d threads"
                          % (",".join(str(n) for n, _ in runs), dt, threads),
                "per_n_terms_per_s": {str(n): 2 ** (n - 1) / t for n, t in runs}}
+        nlast, tlast = runs[-1]
+        cpu["extrapolated_s_per_permanent"] = {
+            str(n): tlast * 2.0 ** (n - nlast) for n in (36, 40) if n > nlast}
+        cpu["extrapolated_note"] = "x2 per +1 in n from the n = %d time (not measured)" % nlast
+        cpu["quad_ryser_s"] = quad_ryser_times([20, 22], threads)
     forms = None
     if world == 1 and not args.no_forms:
         forms = measure_forms(dev, value, peak_fp64, not args.no_large)
