@@ -2,7 +2,7 @@
 //
 // Pipeline (all on the device, so the whole sequence can be captured in one
 // CUDA graph):
-//   0. batch_mult_kernel   per item (Glynn, R0-R3): finds bitwise-identical
+//   0. batch_mult_kernel   per item (Glynn, R0-R2): finds bitwise-identical
 //                          columns (photon collisions, t_j > 1 in Eq. (1)); an
 //                          item with repeated columns walks the multiplicity
 //                          expansion of Eq. (S2) (prod (m_c + 1) x 2^free terms
@@ -86,7 +86,7 @@ struct BatchArgs {
   long long* terms;      // [count]: index-space size of each item (set by batch_mult_kernel)
   MultInfo* mult;        // [count]: column structure; g = 0 for an item without repeated columns
   signed char* mcol;     // [count][BATCH_MAX_N]: original column of distinct column c
-  int use_mult;          // Glynn R0-R3: walk items with repeated columns by the multiplicity expansion
+  int use_mult;          // Glynn R0-R2: walk items with repeated columns by the multiplicity expansion
   double2* prep;
   long long units_cap;
   long long prep_cap;
@@ -99,8 +99,8 @@ struct BatchArgs {
 enum { BATCH_OK = 0, BATCH_BAD_N = 1, BATCH_NO_ROOM = 2 };
 
 // One lane's walk over [kb, ke) of an item of size n: the plain Gray walk, or
-// (mi != nullptr) the multiplicity expansion, whose class-weighted chunk sums go
-// to (tr, ti).
+// (mi != nullptr, rungs R0-R2) the multiplicity expansion, whose class-weighted
+// chunk sums go to (tr, ti).
 template <int PREC, int TUNE>
 __device__ __forceinline__ void batch_walk_n(int n, const double2* Acol, const double2* Step, bool glynn,
                                              const MultInfo* mi, dd* tr, dd* ti, uint64_t kb, uint64_t ke, uint64_t CH,
@@ -110,6 +110,9 @@ __device__ __forceinline__ void batch_walk_n(int n, const double2* Acol, const d
   case N:                                                                                                  \
     if constexpr (PREC == 4) {                                                                             \
       walk_range_df<N>(Acol, reinterpret_cast<const float4*>(Step), N, kb, ke, CH, ar, ai);                \
+    } else if constexpr (PREC == 3) {                                                                      \
+      walk_range<N, PREC, TUNE, true>(Acol, Step, nullptr, nullptr, nullptr, nullptr, N,                   \
+                                      glynn ? KIND_GLYNN : KIND_RYSER, kb, ke, CH, nz, ar, ai, cr, ci);     \
     } else {                                                                                               \
       if (mi != nullptr)                                                                                   \
         walk_range<N, PREC, TUNE, true>(Acol, Step, nullptr, mi, tr, ti, N, KIND_GLYNN_MULT, kb, ke, CH,   \

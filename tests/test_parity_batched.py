@@ -169,7 +169,7 @@ def _repeated(n, mult, seed):
 def test_batched_repeated_columns_every_structure(pg, prec):
     """Items with repeated columns (a pair, a triple, several pairs, no singleton
     at all, every column equal) walk the multiplicity expansion inside the
-    batch (R0-R3; R4 walks the expanded matrix); mixed with plain items, each
+    batch (R0-R2; R3 and R4 walk the expanded matrix); mixed with plain items, each
     against the oracle on the expanded matrix."""
     cases = [(6, [2, 1, 1, 1, 1]), (9, [3, 1, 1, 1, 1, 1, 1]), (12, [2, 2, 2] + [1] * 6), (8, [2, 2, 2, 2]),
              (7, [7]), (10, [4, 3, 1, 1, 1]), (13, [2] + [1] * 11), (5, [1, 1, 1, 1, 1]), (14, [3, 3, 2] + [1] * 6),
