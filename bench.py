@@ -414,6 +414,14 @@ def measure_forms(dev, plain_rate, peak_fp64, large=True):
         lap = float(np.max(np.abs(np.sum(A0 * M[0].cpu().numpy(), axis=1) - P0)) / abs(P0))
         forms["adjoint_64_n24"] = {"terms_per_s": 64 * 2 ** 23 / tg, "s": tg, "cost_vs_plain_same_batch": tg / tf,
                                    "laplace_identity_rel_err": lap}
+        # the same batch with the products in double-float (R3)
+        pg.grad(G[:1], prec="fp64_df")
+        tr3 = timed(lambda: pg.grad(G, prec="fp64_df"))
+        _, _, M3, _ = pg.grad(G[:1], prec="fp64_df")
+        forms["adjoint_64_n24_fp64_df"] = {
+            "terms_per_s": 64 * 2 ** 23 / tr3, "s": tr3, "vs_fp64_adjoint": tg / tr3,
+            "minors_normwise_diff_vs_fp64": float(np.max(np.abs(M3[0].cpu().numpy() - M[0].cpu().numpy()))
+                                                  / np.max(np.abs(M[0].cpu().numpy())))}
         # the same batch through the autograd Function: |Per|^2 forward, gradient backward
         Gr = G.clone().requires_grad_(True)
 

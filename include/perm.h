@@ -204,7 +204,10 @@ int prob_sample(const perm_c128* dU, int m, int ldu, const int32_t* hS, const in
 /* Per(A_b) and its derivatives for a batch of matrices, in the same Gray-code
  * pass as the Glynn sum (Supp. Eq. (S2) of arXiv 1606.05836, differentiated:
  * dPer/da_ij = 2^-(n-1) sum_delta (prod delta) delta_j prod_{k != i} v_k; the
- * paper itself has no gradient).  Plain FP64 (opts->prec must be PERM_FP64).
+ * paper itself has no gradient).  opts->prec PERM_FP64 (default) or PERM_FP64_DF
+ * (the prefix, suffix and q products in double-float on the FP32 pipe; row sums,
+ * the running sums S, the accumulators H and the flips stay FP64); other values
+ * give PERM_EINVAL.  Two adjacent lanes share each Gray walk, half the rows each.
  *
  * dA:        batch matrices, matrix b at dA + b*strideA (complex elements), lda >= n.
  * dPerm:     nullable [batch] Per(A_b).   dAbs2: nullable [batch] |Per(A_b)|^2.

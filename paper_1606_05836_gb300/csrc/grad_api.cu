@@ -76,11 +76,11 @@ int gfail(int e) {
   X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) X(17) X(18) X(19) \
   X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30) X(31) X(32)
 
-int dispatch_grad(int n, const GradArgs& a, int grid, cudaStream_t s) {
+int dispatch_grad(int n, const GradArgs& a, int prec, int grid, cudaStream_t s) {
   switch (n) {
 #define PERM_GC(N) \
   case N:          \
-    return launch_grad<N>(a, grid, s);
+    return launch_grad<N>(a, prec, grid, s);
     PERM_G_CASES(PERM_GC)
 #undef PERM_GC
     default:
@@ -88,11 +88,11 @@ int dispatch_grad(int n, const GradArgs& a, int grid, cudaStream_t s) {
   }
 }
 
-int dispatch_grad_occupancy(int n, int* out) {
+int dispatch_grad_occupancy(int n, int prec, int* out) {
   switch (n) {
 #define PERM_GC(N) \
   case N:          \
-    return grad_blocks_per_sm<N>(out);
+    return grad_blocks_per_sm<N>(prec, out);
     PERM_G_CASES(PERM_GC)
 #undef PERM_GC
     default:
@@ -103,14 +103,15 @@ int dispatch_grad_occupancy(int n, int* out) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct GradLayout {
-  int grid, chunk_log2;
+  int grid, chunk_log2, prec;
   long long P;
   size_t scale_exp, partials, state, total;
 };
 
 int grad_layout(int n, const perm_opts* o, GradLayout* L) {
   if (n < 1 || n > PERM_GRAD_MAX_N) return PERM_ERANGE;
-  if (o && o->prec != PERM_FP64) return PERM_EINVAL;
+  L->prec = o ? o->prec : PERM_FP64;
+  if (L->prec != PERM_FP64 && L->prec != PERM_FP64_DF) return PERM_EINVAL;
   if (o && o->block != 0 && o->block != GRAD_BLOCK) return PERM_EINVAL;
   L->chunk_log2 = (o && o->chunk_log2) ? o->chunk_log2 : 12;
   if (L->chunk_log2 < 1 || L->chunk_log2 > 30) return PERM_EINVAL;
@@ -122,7 +123,7 @@ int grad_layout(int n, const perm_opts* o, GradLayout* L) {
     if (e != cudaSuccess) return gfail((int)e);
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return gfail((int)e);
-    int oe = dispatch_grad_occupancy(n, &bps);
+    int oe = dispatch_grad_occupancy(n, L->prec, &bps);
     if (oe) return gfail(oe);
     if (bps < 1) return gfail((int)cudaErrorInvalidConfiguration);
     grid = sms * bps;
@@ -195,7 +196,7 @@ int perm_grad(const perm_c128* dA, int n, int lda, int batch, int64_t strideA, p
     a.P = L.P;
     a.partials = (double*)(w + L.partials);
     a.scale_exp = (int*)(w + L.scale_exp);
-    int le = dispatch_grad(n, a, L.grid, s);
+    int le = dispatch_grad(n, a, L.prec, L.grid, s);
     if (le) return gfail(le);
     GradReduceArgs r;
     r.state = a.state;

@@ -8,30 +8,41 @@
 
 namespace permk {
 
-template <int N>
-int launch_grad(const GradArgs& a, int grid, cudaStream_t s) {
+template <int N, int PREC>
+static int launch_one(const GradArgs& a, int grid, cudaStream_t s) {
   const size_t smem = grad_smem_bytes(N);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(grad_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(grad_kernel<N, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
   }
-  grad_kernel<N><<<grid, GRAD_BLOCK, smem, s>>>(a);
+  grad_kernel<N, PREC><<<grid, GRAD_BLOCK, smem, s>>>(a);
   return (int)cudaGetLastError();
 }
 
-template <int N>
-int grad_blocks_per_sm(int* out) {
+template <int N, int PREC>
+static int occupancy_one(int* out) {
   const size_t smem = grad_smem_bytes(N);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(grad_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(grad_kernel<N, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
   }
-  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, grad_kernel<N>, GRAD_BLOCK, smem);
+  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, grad_kernel<N, PREC>, GRAD_BLOCK, smem);
 }
 
-#define PERM_GINST(N)                                                   \
-  template int launch_grad<N>(const GradArgs&, int, cudaStream_t); \
-  template int grad_blocks_per_sm<N>(int*);
+// prec: 0 = FP64 (PERM_FP64), 3 = double-float products (PERM_FP64_DF)
+template <int N>
+int launch_grad(const GradArgs& a, int prec, int grid, cudaStream_t s) {
+  return prec == 3 ? launch_one<N, 3>(a, grid, s) : launch_one<N, 0>(a, grid, s);
+}
+
+template <int N>
+int grad_blocks_per_sm(int prec, int* out) {
+  return prec == 3 ? occupancy_one<N, 3>(out) : occupancy_one<N, 0>(out);
+}
+
+#define PERM_GINST(N)                                                        \
+  template int launch_grad<N>(const GradArgs&, int, int, cudaStream_t); \
+  template int grad_blocks_per_sm<N>(int, int*);
 
 #if PERM_PART == 0
 PERM_GINST(1) PERM_GINST(2) PERM_GINST(3) PERM_GINST(4) PERM_GINST(5) PERM_GINST(6) PERM_GINST(7) PERM_GINST(8)

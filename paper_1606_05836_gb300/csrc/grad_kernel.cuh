@@ -99,7 +99,9 @@ __device__ __forceinline__ double2* hstate(const GradArgs& a, int i, int j, long
   return a.state + (long long)(i * N + j) * a.P + p;
 }
 
-template <int N>
+// PREC 0: FP64 throughout; PREC 3 (R3): the prefix / suffix / q products in
+// double-float on the FP32 pipe, row sums, S, H and the accumulation in FP64.
+template <int N, int PREC>
 __global__ void __launch_bounds__(GRAD_BLOCK, 1) grad_kernel(GradArgs a) {
   extern __shared__ double2 smem[];
   constexpr int M = GradShape<N>::M;
@@ -179,41 +181,84 @@ __global__ void __launch_bounds__(GRAD_BLOCK, 1) grad_kernel(GradArgs a) {
         cp_async_commit();
       }
       const unsigned long long smask = (k & 1ull) << 63;  // (prod delta) = (-1)^(k & 1)
-      // suffix products of the half, suf_r = v_r ... v_{M-1}, down to the half's product
-      double pr = vr[M - 1], pi = vi[M - 1];
-      if (M > 1) suf[(M - 1) * B] = make_double2(pr, pi);
+      if constexpr (PREC == 3) {
+        // the products in double-float on the FP32 pipe (each FP64 row sum split
+        // into two FP32 halves, ~48 bits); S, the flips and the row sums stay FP64
+        df dr[M], di[M];
 #pragma unroll
-      for (int r = M - 2; r >= 1; r--) {
-        cmul_inplace<3>(pr, pi, vr[r], vi[r], nz);
-        suf[r * B] = make_double2(pr, pi);
-      }
-      if (M > 1) cmul_inplace<3>(pr, pi, vr[0], vi[0], nz);
-      // the partner's half product; the prefix chain starts from (prod delta) x it,
-      // so S_r += (prod delta) q_r = e suf_{r+1} is one complex multiply-add
-      const double opr = __shfl_xor_sync(pair_mask, pr, 1);
-      const double opi = __shfl_xor_sync(pair_mask, pi, 1);
-      double er = xor_sign(opr, smask), ei = xor_sign(opi, smask);
+        for (int r = 0; r < M; r++) {
+          dr[r] = f64_to_df(vr[r]);
+          di[r] = f64_to_df(vi[r]);
+        }
+        float4* sufF = reinterpret_cast<float4*>(suf);
+        df pr = dr[M - 1], pi = di[M - 1];
+        if (M > 1) sufF[(M - 1) * B] = make_float4(pr.h, pr.l, pi.h, pi.l);
 #pragma unroll
-      for (int r = 0; r < M - 1; r++) {
-        const double2 sf = suf[(r + 1) * B];
-        double2 si = S[r * B];
-        si.x = fma(er, sf.x, si.x);
-        si.x = fma(-ei, sf.y, si.x);
-        si.y = fma(er, sf.y, si.y);
-        si.y = fma(ei, sf.x, si.y);
-        S[r * B] = si;
-        cmul_inplace<3>(er, ei, vr[r], vi[r], nz);
+        for (int r = M - 2; r >= 1; r--) {
+          dfc_mul(pr, pi, dr[r], di[r]);
+          sufF[r * B] = make_float4(pr.h, pr.l, pi.h, pi.l);
+        }
+        if (M > 1) dfc_mul(pr, pi, dr[0], di[0]);
+        const unsigned fs = (unsigned)(k & 1ull) << 31;  // the term's sign on FP32 bit patterns
+        df er{__uint_as_float(__float_as_uint(__shfl_xor_sync(pair_mask, pr.h, 1)) ^ fs),
+              __uint_as_float(__float_as_uint(__shfl_xor_sync(pair_mask, pr.l, 1)) ^ fs)};
+        df ei{__uint_as_float(__float_as_uint(__shfl_xor_sync(pair_mask, pi.h, 1)) ^ fs),
+              __uint_as_float(__float_as_uint(__shfl_xor_sync(pair_mask, pi.l, 1)) ^ fs)};
+#pragma unroll
+        for (int r = 0; r < M - 1; r++) {
+          const float4 sf = sufF[(r + 1) * B];
+          df tr = er, ti = ei;
+          dfc_mul(tr, ti, df{sf.x, sf.y}, df{sf.z, sf.w});
+          double2 si = S[r * B];
+          si.x += f32_to_f64_int(tr.h) + f32_to_f64_int(tr.l);
+          si.y += f32_to_f64_int(ti.h) + f32_to_f64_int(ti.l);
+          S[r * B] = si;
+          dfc_mul(er, ei, dr[r], di[r]);
+        }
+        double2 sl = S[(M - 1) * B];
+        sl.x += f32_to_f64_int(er.h) + f32_to_f64_int(er.l);
+        sl.y += f32_to_f64_int(ei.h) + f32_to_f64_int(ei.l);
+        S[(M - 1) * B] = sl;
+        dfc_mul(er, ei, dr[M - 1], di[M - 1]);
+        ar += f32_to_f64_int(er.h) + f32_to_f64_int(er.l);
+        ai += f32_to_f64_int(ei.h) + f32_to_f64_int(ei.l);
+      } else {
+        // suffix products of the half, suf_r = v_r ... v_{M-1}, down to the half's product
+        double pr = vr[M - 1], pi = vi[M - 1];
+        if (M > 1) suf[(M - 1) * B] = make_double2(pr, pi);
+#pragma unroll
+        for (int r = M - 2; r >= 1; r--) {
+          cmul_inplace<3>(pr, pi, vr[r], vi[r], nz);
+          suf[r * B] = make_double2(pr, pi);
+        }
+        if (M > 1) cmul_inplace<3>(pr, pi, vr[0], vi[0], nz);
+        // the partner's half product; the prefix chain starts from (prod delta) x it,
+        // so S_r += (prod delta) q_r = e suf_{r+1} is one complex multiply-add
+        const double opr = __shfl_xor_sync(pair_mask, pr, 1);
+        const double opi = __shfl_xor_sync(pair_mask, pi, 1);
+        double er = xor_sign(opr, smask), ei = xor_sign(opi, smask);
+#pragma unroll
+        for (int r = 0; r < M - 1; r++) {
+          const double2 sf = suf[(r + 1) * B];
+          double2 si = S[r * B];
+          si.x = fma(er, sf.x, si.x);
+          si.x = fma(-ei, sf.y, si.x);
+          si.y = fma(er, sf.y, si.y);
+          si.y = fma(ei, sf.x, si.y);
+          S[r * B] = si;
+          cmul_inplace<3>(er, ei, vr[r], vi[r], nz);
+        }
+        // the half's last row: q = e
+        double2 sl = S[(M - 1) * B];
+        sl.x += er;
+        sl.y += ei;
+        S[(M - 1) * B] = sl;
+        // the whole term (prod delta) prod_i v_i = e v_{M-1}, added by both lanes
+        ar = fma(er, vr[M - 1], ar);
+        ar = fma(-ei, vi[M - 1], ar);
+        ai = fma(er, vi[M - 1], ai);
+        ai = fma(ei, vr[M - 1], ai);
       }
-      // the half's last row: q = e
-      double2 sl = S[(M - 1) * B];
-      sl.x += er;
-      sl.y += ei;
-      S[(M - 1) * B] = sl;
-      // the whole term (prod delta) prod_i v_i = e v_{M-1}, added by both lanes
-      ar = fma(er, vr[M - 1], ar);
-      ar = fma(-ei, vi[M - 1], ar);
-      ai = fma(er, vi[M - 1], ai);
-      ai = fma(ei, vr[M - 1], ai);
       ++k;
       if (k >= ke) break;
       // column j = b+1 flips (delta_j -> -delta_j): H_:j += 2 delta_j^old S
@@ -294,9 +339,9 @@ struct GradReduceArgs {
 };
 
 template <int N>
-int launch_grad(const GradArgs& a, int grid, cudaStream_t s);
+int launch_grad(const GradArgs& a, int prec, int grid, cudaStream_t s);
 template <int N>
-int grad_blocks_per_sm(int* out);
+int grad_blocks_per_sm(int prec, int* out);
 
 // dynamic shared memory: the staged matrix (n columns of stride NP), then per lane
 // the half's suffix products, S and (n >= 16) the prefetched H column

@@ -13,15 +13,18 @@ import ctypes
 import torch
 
 from . import _native
-from ._native import Opts
+from ._native import PRECISIONS, Opts
 from ._workspace import workspace as _workspace
 
 PERM_GRAD_MAX_N = 32
 
 
-def grad(A: torch.Tensor, minor: bool = True, grad_abs2: bool = False, chunk_log2: int = 0, grid: int = 0):
+def grad(A: torch.Tensor, minor: bool = True, grad_abs2: bool = False, chunk_log2: int = 0, grid: int = 0,
+         prec: str = "fp64"):
     """Per(A_b), |Per(A_b)|^2 and, on request, dPer/da_ij and 2 Per conj(dPer/da_ij).
 
+    prec: "fp64" (default) or "fp64_df" (the products in double-float on the FP32
+    pipe; row sums, accumulators and the flips in FP64).
     Returns (per[batch], abs2[batch], minor[batch, n, n] or None, grad_abs2[batch, n, n] or None);
     a 2-D input gives 0-dim / 2-D results.
     """
@@ -38,7 +41,9 @@ def grad(A: torch.Tensor, minor: bool = True, grad_abs2: bool = False, chunk_log
     if n > PERM_GRAD_MAX_N:
         raise ValueError("perm_grad supports n <= %d" % PERM_GRAD_MAX_N)
     dev = A.device
-    o = Opts(0, int(chunk_log2), 0, int(grid), 0)
+    if prec not in ("fp64", "fp64_df"):
+        raise ValueError("perm_grad supports prec 'fp64' and 'fp64_df'")
+    o = Opts(PRECISIONS[prec], int(chunk_log2), 0, int(grid), 0)
     per = torch.empty(batch, dtype=torch.complex128, device=dev)
     abs2 = torch.empty(batch, dtype=torch.float64, device=dev)
     M = torch.empty(batch, n, n, dtype=torch.complex128, device=dev) if minor else None

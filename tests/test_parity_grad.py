@@ -118,3 +118,44 @@ def test_autograd_function(pg):
         Ab = mats[b].detach().cpu().numpy()
         want = w[b].item() * 2 * oracle.ryser(Ab).hi * np.conj(oracle.minors(Ab))
         assert normwise(mats.grad[b].cpu().numpy(), want) < 2 * REL_TOL
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 8, 14, 17])
+def test_minors_vs_oracle_double_float_products(pg, n):
+    """The R3 adjoint (prefix / suffix / q products in double-float on the FP32
+    pipe, row sums and accumulators FP64) against the oracle's minors: the same
+    1e-10 bar as the FP64 adjoint."""
+    A = S.gaussian(n, 980 + n, 1.0)
+    per, abs2, M, G = pg.grad(to_dev(A), minor=True, grad_abs2=True, prec="fp64_df")
+    want_p = oracle.ryser(A)
+    assert want_p.rel_err(complex(per.cpu().item())) < REL_TOL
+    if n == 1:
+        assert complex(M.cpu()[0, 0].item()) == 1.0
+        return
+    W = oracle.minors(A)
+    assert normwise(M.cpu().numpy(), W) < REL_TOL
+    assert normwise(G.cpu().numpy(), 2 * want_p.hi * np.conj(W)) < 2 * REL_TOL
+
+
+@pytest.mark.parametrize("n", [24, 32])
+def test_double_float_products_full_size(pg, n):
+    """R3 adjoint at the configured sizes: the Laplace identities, and agreement
+    with the FP64 adjoint's minors (normwise) and permanent."""
+    A = S.gaussian(n, 990 + n)
+    dA = to_dev(A)
+    per, _, M, _ = pg.grad(dA, prec="fp64_df")
+    per0, _, M0, _ = pg.grad(dA)
+    M, M0 = M.cpu().numpy(), M0.cpu().numpy()
+    P = complex(per.cpu().item())
+    assert np.max(np.abs(np.sum(A * M, axis=1) - P)) <= REL_TOL * abs(P) * 10
+    assert normwise(M, M0) < REL_TOL
+    assert abs(P - complex(per0.cpu().item())) <= REL_TOL * abs(P)
+
+
+def test_grad_rejects_other_precisions(pg):
+    with pytest.raises(ValueError):
+        pg.grad(to_dev(S.gaussian(4, 1, 1.0)), prec="fp32x2")
+    import ctypes
+    from paper_1606_05836_gb300._native import Opts, load
+    o = Opts(2, 0, 0, 0, 0)
+    assert load().perm_grad_workspace_size(4, ctypes.byref(o)) == 0
