@@ -217,3 +217,41 @@ def test_logical_item_shards_on_one_gpu():
         for i, v in zip(p, fn([mats[i] for i in p])):
             out[i] = v
     assert out == whole
+
+
+def _gpu_rank_main(rank, world, port, n, q):
+    import torch
+    import torch.distributed as dist
+    from paper_1606_05836_gb300.shard import gpu_partial_fn
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    dA = torch.as_tensor(S.gaussian(n, 88)).cuda()
+    q.put((rank, sharded_permanent(n, "glynn", gpu_partial_fn(dA, "glynn"), rank, world)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.gpu
+def test_two_processes_share_one_permanent_on_the_gpu():
+    """The sharded path end to end with real processes: two ranks (gloo for the
+    exchange of partials) each sum their half of the Gray range with the GPU range
+    kernel, and perm_combine_partials on every rank gives the single launch's
+    value.  (Both processes use this box's one GPU; their kernels never wait on
+    each other.)"""
+    import torch
+    import paper_1606_05836_gb300 as pg
+    n, world = 26, 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_gpu_rank_main, args=(r, world, port, n, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    got = dict(q.get(timeout=10) for _ in range(world))
+    single = complex(pg.glynn(torch.as_tensor(S.gaussian(n, 88)).cuda()).cpu().item())
+    assert got[0] == got[1]
+    assert abs(got[0] - single) <= 1e-12 * abs(single)
