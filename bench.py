@@ -80,6 +80,7 @@ def parse_args():
     ap.add_argument("--batched-count", type=int, default=4096)
     ap.add_argument("--adjoint-n", type=int, default=24)
     ap.add_argument("--adjoint-batch", type=int, default=64)
+    ap.add_argument("--adjoint-prec", default="fp64", choices=["fp64", "fp64_df"])
     ap.add_argument("--sampler-m", type=int, default=1000)
     ap.add_argument("--sampler-n", type=int, default=24)
     ap.add_argument("--sampler-count", type=int, default=16)
@@ -933,16 +934,16 @@ def run_single_form(args):
         n, b = args.adjoint_n, args.adjoint_batch
         G = torch.as_tensor(np.stack([S.gaussian(n, i) for i in range(b)])).to(dev)
         for _ in range(args.warmup):
-            pg.grad(G[:1])
+            pg.grad(G[:1], prec=args.adjoint_prec)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(args.steps):
-            pg.grad(G)
+            pg.grad(G, prec=args.adjoint_prec)
         e1.record()
         torch.cuda.synchronize(dev)
         t = e0.elapsed_time(e1) / 1e3
-        print(json.dumps({"form": "adjoint", "n": n, "batch": b, "steps": args.steps,
+        print(json.dumps({"form": "adjoint", "n": n, "batch": b, "steps": args.steps, "prec": args.adjoint_prec,
                           "terms_per_s": args.steps * b * 2 ** (n - 1) / t}), flush=True)
     else:
         import math
